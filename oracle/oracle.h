@@ -1,0 +1,161 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle for the parallel Monte Carlo closed-loop
+ * study of Kaysfeld, Zanon and Joergensen (arXiv 2212.02197).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path; only
+ * the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+ * load it.  It shares no source, header, table or helper with the CUDA path:
+ * configuration reaches it as plain data through the structs below.
+ *
+ * Everything is straightforward double-precision C, one trajectory at a time,
+ * in the order and notation of the paper:
+ *   Sec. II   stochastic continuous-discrete system, Eq. (CDS)
+ *   Sec. III  CD-EKF prediction (predictionEquations) and filtering (Josph),
+ *             regulator OCP (OPC_general) and its multiple-shooting NLP (OCP_NLP)
+ *   Sec. IV   SQP: QP subproblem (QP-subproblem), Powell l1-merit backtracking
+ *             line search (Armijo), damped block BFGS, scaled convergence test
+ *   Sec. V    PI controller with anti-windup, Eq. (PI)
+ *   Sec. VI   CSTR model, Eq. (CSTR), three-state plant and one-state model
+ *   Sec. VII  closed-loop set-up and the performance index, Eq. (Phi)
+ *
+ * The QP subproblem is solved here by condensing the state increments away
+ * and running a dense primal active-set method to the exact KKT point; the
+ * paper's solver (a Riccati interior-point method) is deliberately not used,
+ * so that the GPU path and this oracle reach the unique QP minimiser by
+ * independent routes.
+ *
+ * Pins for every function are in tests/test_oracle_*.py.
+ */
+#ifndef MC_ORACLE_H
+#define MC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_SP 16   /* set-point schedule segments            */
+#define OR_MAX_N 64    /* longest prediction horizon supported   */
+
+/* Plant and NMPC model (Sec. VI) plus the closed-loop set-up (Sec. VII).
+ * Units: s, L, mol, K.  The state of the plant is n = c V (mol, mol, K L). */
+typedef struct {
+  double V, k0, EaR, beta, cA_in, cB_in, T_in;
+  double sigma[3];      /* diagonal of sigma-bar, (mol/L, mol/L, K)          */
+  double meas_sd;       /* square root of the measurement covariance R (K)   */
+  double Ts, t0;        /* sample time and start time (s)                    */
+  int32_t n_steps;      /* control steps K; Phi has K+1 terms                */
+  int32_t n_em;         /* Euler-Maruyama substeps per sample, N_s           */
+  int32_t n_sp;         /* number of set-point segments                      */
+  int32_t pad0;
+  double sp_time[OR_MAX_SP];   /* segment s starts at sp_time[s]             */
+  double sp_value[OR_MAX_SP];  /* set-point temperature of segment s (K)     */
+  double Ea_logsd;      /* per-trajectory lognormal sd of E_a/R, 0 = off    */
+  double dTin_step;     /* magnitude of the inlet-temperature step, 0 = off */
+} or_model;
+
+/* Controller: NMPC (Sec. III, IV) or PI (Sec. V). */
+typedef struct {
+  int32_t kind;         /* 0 = NMPC, 1 = PI                                  */
+  int32_t N;            /* prediction horizon (control intervals)            */
+  int32_t n_rk4;        /* classical RK4 steps per interval, N_c             */
+  int32_t sqp_max_it;   /* SQP iteration limit                               */
+  int32_t ls_max;       /* maximum number of step halvings                   */
+  int32_t pad0;
+  double u_min, u_max;  /* input bounds (mL/min)                             */
+  double kP, kI, kaw;   /* PI gains, acting on F in L/s and e in K           */
+  double Qz;            /* output weight of the NMPC objective               */
+  double P0;            /* initial EKF covariance P_{-1|-1} ((K L)^2)        */
+  double sqp_tol;       /* epsilon of the scaled convergence test            */
+  double u_scale;       /* unit of the OCP input variable, in mL/min         */
+  double x_scale;       /* unit of the OCP state variable, in K L            */
+} or_ctrl;
+
+/* Per-trajectory result of one closed-loop simulation. */
+typedef struct {
+  double phi;            /* performance index, Eq. (Phi)                     */
+  int32_t n_ocp;         /* OCPs solved (= K for NMPC)                       */
+  int32_t n_ocp_failed;  /* OCPs that hit the SQP iteration limit            */
+  int32_t sqp_iters;     /* QP subproblems solved, summed over the OCPs      */
+  int32_t ls_trials;     /* merit evaluations in the line searches           */
+  int32_t n_hess_reset;  /* block-BFGS resets to the identity                */
+  int32_t n_ls_fail;     /* line searches that ran out of halvings           */
+  int32_t qp_iters;      /* active-set iterations, summed                    */
+  int32_t nonfinite;     /* 1 if the state became non-finite                 */
+} or_traj_out;
+
+/* Per-OCP diagnostics of one SQP solve. */
+typedef struct {
+  int32_t iters;         /* QP subproblems solved                            */
+  int32_t status;        /* 0 converged, 1 iteration limit, 2 line search    */
+  int32_t ls_trials;
+  int32_t n_hess_reset;
+  int32_t qp_iters;
+  int32_t pad0;
+  double kkt_grad;       /* ||grad L / s_d||_inf at the returned point       */
+  double kkt_eq;         /* ||g||_inf at the returned point                  */
+  double f;              /* objective at the returned point                  */
+} or_sqp_info;
+
+/* ---- counter-based random numbers (Philox4x32-10, Salmon et al. SC'11) ---- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_uniform52(uint32_t hi, uint32_t lo);
+void or_normal_pair(const uint32_t w[4], double z[2]);
+/* normals used by the closed loop: tag 0/1 process noise, 2 measurement, 3 params */
+void or_process_noise(uint64_t seed, int64_t j, int64_t substep, double xi[3]);
+double or_meas_noise(uint64_t seed, int64_t j, int64_t step);
+void or_traj_params(const or_model* m, uint64_t seed, int64_t j,
+                    double* EaR_j, double* t_d, double* dTin);
+
+/* ---- CSTR model, Eq. (CSTR) ---- */
+void or_plant_drift(const or_model* m, double EaR, double T_in, const double n[3],
+                    double F, double f[3]);
+void or_model1(const or_model* m, double EaR, double x, double F,
+               double* f, double* fx, double* fF);
+double or_zbar(const or_model* m, double t);
+double or_Fss(const or_model* m, double EaR, double Tbar);
+void or_em_step(const or_model* m, double EaR, double T_in, double n[3], double F,
+                double h, const double xi[3]);
+
+/* ---- one shooting interval with classical RK4 and forward sensitivities ---- */
+void or_rk4_interval(const or_model* m, double EaR, int n_rk4, double Ts, double x0,
+                     double F, double Fconv, double* xF, double* A, double* B);
+
+/* ---- CD-EKF ---- */
+void or_ekf_predict(const or_model* m, double EaR, int n_rk4, double F, double* x,
+                    double* P);
+void or_ekf_filter(const or_model* m, double y, double* x, double* P,
+                   double* P_short);
+
+/* ---- structured QP subproblem, solved by condensing + primal active set ---- */
+int or_qp_solve(int N, const double* A, const double* B, const double* b,
+                const double* Wxx, const double* Wxu, const double* Wuu,
+                const double* q, const double* r, const double* lb, const double* ub,
+                double* du, double* dx, double* mu, double* nul, double* nuu,
+                int* iters);
+
+/* ---- damped BFGS update of one packed 1x1 or 2x2 Hessian block ---- */
+void or_bfgs_block(int n, double* w, const double* s, const double* y);
+
+/* ---- SQP for one OCP; warm start in u, x, lam, pil, piu (updated in place) ---- */
+int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
+           const double* zbar /* zbar[k], k = 1..N */, double* u, double* x,
+           double* lam, double* pil, double* piu, or_sqp_info* info);
+
+/* ---- PI controller, Eq. (PI) ---- */
+double or_pi_step(const or_ctrl* c, double Ts, double ybar, double y, double ubar,
+                  double* Ihat);
+
+/* ---- closed loop and Monte Carlo driver ---- */
+/* trace (optional, may be NULL): per step i = 0..K-1 the row
+ * (T_plant, y, xhat, u_applied_mLmin, sqp_iters)                        */
+void or_traj(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j,
+             or_traj_out* out, double* trace);
+void or_run(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j0,
+            int64_t j1, int n_threads, or_traj_out* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

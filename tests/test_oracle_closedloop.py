@@ -1,0 +1,113 @@
+"""Closed-loop checks of the oracle (Sec. VII): counting identities of Table II,
+the qualitative result of Sec. VII-C (NMPC beats PI in mean and variance of
+Phi), common random numbers, and independence of the result from how the
+trajectories are split over threads."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_02197_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = W.get("cstr_100x120_N20_fp64")
+    n = 32
+    r_n = oracle.run(w["model"], w["nmpc"], w["seed"], 0, n)
+    r_p = oracle.run(w["model"], w["pi"], w["seed"], 0, n)
+    return w, r_n, r_p
+
+
+def test_total_ocps_equals_trajectories_times_steps(small):
+    w, r_n, r_p = small
+    K = w["model"]["n_steps"]
+    assert np.all(r_n["n_ocp"] == K)
+    assert r_n["n_ocp"].sum() == len(r_n["phi"]) * K
+    assert np.all(r_p["n_ocp"] == 0)
+
+
+def test_nmpc_outperforms_pi_in_mean_and_variance(small):
+    _, r_n, r_p = small
+    assert r_n["phi"].mean() < r_p["phi"].mean()
+    assert r_n["phi"].var() < r_p["phi"].var()
+    assert np.all(np.isfinite(r_n["phi"])) and np.all(np.isfinite(r_p["phi"]))
+
+
+def test_failed_ocp_fraction_is_small():
+    """Table II: a tiny fraction of the OCPs hits the iteration limit."""
+    w = W.get("cstr_30k_x240_N20_fp64")
+    r = oracle.run(w["model"], w["nmpc"], w["seed"], 0, 24)
+    frac = r["n_ocp_failed"].sum() / r["n_ocp"].sum()
+    assert frac < 1e-3
+    assert r["n_ls_fail"].sum() == 0
+
+
+def test_split_and_thread_count_do_not_change_results():
+    w = W.get("cstr_100x120_N20_fp64")
+    one = oracle.run(w["model"], w["nmpc"], w["seed"], 0, 12, threads=1)
+    a = oracle.run(w["model"], w["nmpc"], w["seed"], 0, 5, threads=3)
+    b = oracle.run(w["model"], w["nmpc"], w["seed"], 5, 12, threads=2)
+    for f in oracle.TRAJ_FIELDS:
+        assert np.array_equal(one[f], np.concatenate([a[f], b[f]]))
+
+
+def test_common_random_numbers_between_controllers():
+    """NMPC and PI trajectories with the same seed and index see the same
+    measurement noise: their first measurements coincide."""
+    w = W.get("cstr_100x120_N20_fp64")
+    for j in (0, 7):
+        tn = oracle.traj(w["model"], w["nmpc"], w["seed"], j, with_trace=True)["trace"]
+        tp = oracle.traj(w["model"], w["pi"], w["seed"], j, with_trace=True)["trace"]
+        assert tn[0, 0] == tp[0, 0] and tn[0, 1] == tp[0, 1]
+    a = oracle.traj(w["model"], w["pi"], w["seed"], 0)["phi"]
+    b = oracle.traj(w["model"], w["pi"], w["seed"], 1)["phi"]
+    assert a != b
+
+
+def test_noise_free_nmpc_tracks_all_setpoints():
+    """Sec. VII-A: the NMPC tracks stable and unstable steady states.  With
+    negligible noise the plant settles at each reachable set-point."""
+    w = W.get("cstr_30k_x240_N20_fp64")
+    m = dict(w["model"])
+    m["sigma"] = [1e-9, 1e-9, 1e-9]
+    m["meas_sd"] = 1e-6
+    m["dTin_step"] = 0.0
+    tr = oracle.traj(m, w["nmpc"], w["seed"], 0, with_trace=True)["trace"]
+    Tplant = tr[:, 0]
+    # the unstable 290 K steady state is held from 50 s until the 340 K set-point
+    # enters the 10 s horizon at 70 s; 340 K is held from 100 s to the end
+    assert np.all(np.abs(Tplant[100:140] - 290.0) < 0.02)
+    assert np.all(np.abs(Tplant[200:240] - 340.0) < 0.02)
+    # the 282 K set-point is reached before the anticipation of 290 K begins
+    assert np.min(np.abs(Tplant[60:68] - 282.0)) < 0.1
+
+
+def test_trajectory_parameters():
+    """Inlet-temperature step at a uniform time in [t0, tf) with a +-5 K sign,
+    and a median-preserving lognormal E_a/R."""
+    w = W.get("cstr_30k_x240_N20_fp64")
+    m = w["model"]
+    tds, signs = [], []
+    for j in range(400):
+        EaR, td, dT = oracle.traj_params(m, 3, j)
+        assert EaR == m["EaR"]
+        assert 0.0 <= td < m["n_steps"] * m["Ts"]
+        assert abs(dT) == 5.0
+        tds.append(td)
+        signs.append(dT > 0)
+    assert 0.4 < np.mean(signs) < 0.6
+    assert abs(np.mean(tds) / (m["n_steps"] * m["Ts"]) - 0.5) < 0.06
+    m3 = W.get("cstr_100k_x240_N30_mixed")["model"]
+    logs = np.log([oracle.traj_params(m3, 3, j)[0] / m3["EaR"] for j in range(2000)])
+    assert abs(np.std(logs) - 0.02) < 0.002 and abs(np.mean(logs)) < 0.002
+
+
+def test_degenerate_filter_is_reported_not_hidden():
+    """Without measurement and process noise the filter gain is 0/0; the
+    trajectory is flagged non-finite and its Phi is NaN."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"])
+    m["sigma"] = [0.0, 0.0, 0.0]
+    m["meas_sd"] = 0.0
+    r = oracle.traj(m, w["nmpc"], w["seed"], 0)
+    assert r["nonfinite"] == 1 and np.isnan(r["phi"])
