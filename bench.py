@@ -1,0 +1,347 @@
+"""Benchmark: the paper-scale Monte Carlo closed-loop study on GB300.
+
+One step = the whole hot path on one batch: 30,000 NMPC closed-loop
+trajectories (CD-EKF + SQP per sample) and the 30,000 PI reference
+trajectories on the same noise, 240 control steps each, N = 20, inlet-
+temperature step disturbance, followed by the on-device reduction of Phi and
+the OCP statistics.  value = NMPC closed-loop trajectories per second (the PI
+companion runs inside the same timed step and is not counted).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
+
+--impl reference times the FP64 CPU oracle (the plain C implementation of the
+paper's method) on the host cores, one trajectory per thread at a time, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2212_02197_gb300 import workloads as W  # noqa: E402
+
+METRIC = "closed-loop trajectories/sec (NMPC CSTR, 30k sims) mixed vs FP64, at stated tol"
+DEFAULT_WORKLOAD = "cstr_30k_x240_N20_fp64"
+# nominal FP64 rate of a GB300 (no measured FP64 peak in MEASURED_PEAKS.json)
+FP64_PEAK_TFLOPS = 1.25
+
+
+# ------------------------------------------------------------------ algorithmic work
+
+def nmpc_flops(cfg_model, cfg_ctrl, n_traj, st):
+    """Algorithmic FP64 operations of one NMPC launch (fma = 2, each divide,
+    square root or transcendental = 1), from the counters the kernel reports:
+      RK4 step of the one-state model with sensitivities: 200
+      SQP evaluation (shooting of N intervals):           N * n_rk4 * 200
+      active-set QP iteration (Riccati sweeps, tests):    40 per stage
+      SQP iteration bookkeeping (gradient, KKT, BFGS, merit): 60 per stage
+      CD-EKF prediction (n_rk4 RK4 steps of x and P) + filter: 170 n_rk4 + 15
+      Euler-Maruyama substep incl. two Box-Muller pairs:   60
+    """
+    N, nrk = cfg_ctrl["N"], cfg_ctrl["n_rk4"]
+    K, nem = cfg_model["n_steps"], cfg_model["n_em"]
+    evals = st["n_ocp"] + st["ls_trials"]
+    f = evals * N * nrk * 200.0
+    f += st["qp_iters"] * N * 40.0
+    f += st["sqp_iters"] * N * 60.0
+    f += n_traj * K * (170.0 * nrk + 15.0 + nem * 60.0 + 40.0)
+    return f
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([t.strip() for t in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                mx = float(r[2].split()[0])
+            except Exception:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, workload):
+    """Oracle on the host cores: bounded sample of the workload per step."""
+    import oracle
+
+    oracle.build()
+    w = W.get(workload)
+    cores = os.cpu_count() or 1
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    # sample size: about 10 s of host time per step at most
+    n = 16 * cores
+    t0 = time.perf_counter()
+    oracle.run(w["model"], w["nmpc"], w["seed"], 0, n, threads=cores)
+    if w["pi"] is not None:
+        oracle.run(w["model"], w["pi"], w["seed"], 0, n, threads=cores)
+    dt = time.perf_counter() - t0
+    n = max(cores, min(w["n_traj"], int(n * 8.0 / max(dt, 1e-3))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        j0 = (s * n) % max(1, w["n_traj"] - n)
+        t0 = time.perf_counter()
+        oracle.run(w["model"], w["nmpc"], w["seed"], j0, j0 + n, threads=cores)
+        if w["pi"] is not None:
+            oracle.run(w["model"], w["pi"], w["seed"], j0, j0 + n, threads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n * len(times) / tot
+    sample = (f"{n} NMPC + {n} PI trajectories of {workload} per step "
+              f"({'pthreads, one trajectory per thread at a time'})")
+    return {"metric": METRIC, "value": value, "unit": "trajectories/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "n_traj": n, "oracle": "oracle/ (C, FP64)"},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline(workload, budget_s=15.0):
+    import oracle
+
+    oracle.build()
+    w = W.get(workload)
+    cores = os.cpu_count() or 1
+    n = 8 * cores
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.run(w["model"], w["nmpc"], w["seed"], done, done + n, threads=cores)
+        if w["pi"] is not None:
+            oracle.run(w["model"], w["pi"], w["seed"], done, done + n, threads=cores)
+        done += n
+        if time.perf_counter() - t0 > budget_s or done + n > w["n_traj"]:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+            "sample": f"trajectories 0..{done - 1} of {workload}, NMPC and PI each, "
+                      f"{cores} host threads, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    # smaller cases of the same workload, for profiling captures
+    ap.add_argument("--n-traj", type=int, default=None)
+    ap.add_argument("--n-steps", type=int, default=None)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        line = run_reference(args, args.workload)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2212_02197_gb300 import mc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    w = W.get(args.workload)
+    if args.n_traj:
+        w["n_traj"] = args.n_traj
+    if args.n_steps:
+        w["model"]["n_steps"] = args.n_steps
+    T = w["n_traj"]
+    # weak scaling: rank r simulates trajectories r*T .. (r+1)*T-1
+    j0, j1 = rank * T, (rank + 1) * T
+    h_n = mc.MonteCarlo(w["model"], w["nmpc"], j1, w["seed"])
+    h_p = mc.MonteCarlo(w["model"], w["pi"], j1, w["seed"]) if w["pi"] is not None else None
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        h_n.run(stream, j0, j1)
+        if h_p is not None:
+            h_p.run(stream, j0, j1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    nmpc_ms = []
+    barrier()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (untimed)
+        a, b, c = ev[i]
+        a.record(stream)
+        h_n.run(stream, j0, j1)
+        b.record(stream)
+        if h_p is not None:
+            h_p.run(stream, j0, j1)
+        c.record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    nmpc_ms = [a.elapsed_time(b) for a, b, c in ev]
+    st_n = h_n.stats()
+    my_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([my_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        my_ms = float(t.item())
+    ms_per_step = my_ms / args.steps
+    value = world * T / (ms_per_step / 1e3)
+
+    # dominant kernel: the NMPC closed loop; its device time per launch
+    # (mc_run = k_nmpc + two small reduction kernels)
+    flops = nmpc_flops(w["model"], w["nmpc"], T, st_n)
+    k_ms = statistics.mean(nmpc_ms)
+    achieved = flops / (k_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_nmpc (FP64, one thread per trajectory)",
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak available)"}
+
+    # end to end through the C ABI with host buffers: create (config h2d),
+    # run, stats and Phi copied back to host, destroy
+    e2e_ms = []
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hn = mc.MonteCarlo(w["model"], w["nmpc"], j1, w["seed"])
+        hn.run(stream, j0, j1)
+        hp = None
+        if w["pi"] is not None:
+            hp = mc.MonteCarlo(w["model"], w["pi"], j1, w["seed"])
+            hp.run(stream, j0, j1)
+        phi_n = hn.phi(j0, T)
+        sn = hn.stats()
+        if hp is not None:
+            phi_p = hp.phi(j0, T)
+            hp.stats()
+            hp.close()
+        hn.close()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms_step = statistics.mean(e2e_ms) if e2e_ms else float("nan")
+    if world > 1:
+        t = torch.tensor([e2e_ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms_step = float(t.item())
+    h2d = 2 * (8 * len(w["model"]["sp_time"]) * 2 + 400)
+    d2h = 8 * T * (2 if w["pi"] is not None else 1) + 2 * 2400
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n_traj_nmpc": T,
+                           "n_traj_pi": T if w["pi"] is not None else 0,
+                           "n_steps": w["model"]["n_steps"], "N": w["nmpc"]["N"],
+                           "precision": w["nmpc"]["precision"],
+                           "qp_solver": w["nmpc"]["qp_solver"],
+                           "l2": "512 MB buffer written between timed steps",
+                           "parallelism": f"trajectory shards x{world}"},
+                "nmpc_ms_per_step": statistics.mean(nmpc_ms),
+                "ocp_stats": {k: st_n[k] for k in ("n_ocp", "n_ocp_failed", "n_ls_fail",
+                                                   "sqp_iters", "ls_trials", "qp_iters",
+                                                   "n_hess_reset")},
+                "phi": {"nmpc_mean": st_n["phi_mean"], "nmpc_var": st_n["phi_var"]},
+                "gpu_launches": args.steps * (3 + (3 if h_p is not None else 0)),
+                "roofline": roofline,
+                "clocks": clk, "wall_s_timed": wall,
+                "e2e": {"value": world * T / (e2e_ms_step / 1e3), "unit": "trajectories/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+        if h_p is not None:
+            st_p = h_p.stats()
+            line["phi"].update(pi_mean=st_p["phi_mean"], pi_var=st_p["phi_var"])
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    h_n.close()
+    if h_p is not None:
+        h_p.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

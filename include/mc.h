@@ -1,0 +1,220 @@
+/*
+ * mc.h -- C ABI of the GB300 Monte Carlo closed-loop library.
+ *
+ * The library runs many independent stochastic closed-loop simulations of a
+ * continuous stirred tank reactor (CSTR) on one NVIDIA GB300 GPU, following
+ * Kaysfeld, Zanon, Joergensen, "Performance Quantification of a Nonlinear
+ * Model Predictive Controller by Parallel Monte Carlo Simulations of a
+ * Closed-loop System" (arXiv 2212.02197):
+ *
+ *   plant     three-state CSTR SDE, Eq. (CSTR) of Sec. VI, integrated by
+ *             Euler-Maruyama with N_s substeps per sample (Sec. VII-A),
+ *   sensor    y_i = c_T(t_i) + v_i, v_i ~ N(0, R) (Sec. II, Eq. CDS),
+ *   NMPC      CD-EKF prediction/filtering (Sec. III-A, Eqs. predictionEquations
+ *             and Josph) on the one-state model, and the regulator OCP
+ *             (Eq. OPC_general) in multiple-shooting form (Eq. OCP_NLP),
+ *             solved by SQP (Sec. IV): structured QP subproblem
+ *             (Eq. QP-subproblem), Powell l1-merit backtracking line search
+ *             (Eq. Armijo), damped block BFGS, scaled convergence test
+ *             (Eq. convergence),
+ *   PI        the reference controller with anti-windup, Eq. (PI) of Sec. V,
+ *   result    the performance index Phi of Eq. (Phi), Sec. VII-C, per
+ *             trajectory, plus the OCP statistics of Table II.
+ *
+ * Conventions for every function below:
+ *   - Pointers named *_host are host memory; *_dev are device memory; a
+ *     `dst_is_device` flag says which one a destination is.
+ *   - Nothing aborts.  Every function returns an mc_status; on failure the
+ *     handle (if any) keeps a message available from mc_last_error().
+ *   - The handle owns all device memory it allocates (cudaMalloc in
+ *     mc_create, freed by mc_destroy).  Input arrays are copied at the call,
+ *     so the caller may free them when the call returns.
+ *   - Work is enqueued on the CUDA stream given as `cuda_stream`
+ *     (a cudaStream_t; NULL means the legacy default stream) and is
+ *     asynchronous until mc_stats / mc_copy_* / mc_sync.
+ *   - Units: time s, volume L, amount mol, temperature K; flows at this
+ *     interface in mL/min.
+ */
+#ifndef MC_GB300_H
+#define MC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_MAX_SETPOINTS 16
+#define MC_MAX_HORIZON 64
+#define MC_MAX_BINS 256
+#define MC_N_COUNTERS 8
+
+typedef enum {
+  MC_OK = 0,
+  MC_EINVAL = 1,          /* invalid argument or configuration               */
+  MC_ENOMEM = 2,          /* device allocation failed                        */
+  MC_ECUDA = 3,           /* a CUDA call failed (message in mc_last_error)   */
+  MC_ETIMEOUT = 4,        /* the GPU did not finish within the wait limit    */
+  MC_ENOTRUN = 5,         /* results requested before any mc_run             */
+  MC_WARN_NONFINITE = 100 /* finished; some trajectories became non-finite   */
+} mc_status;
+
+typedef enum { MC_CTRL_NMPC = 0, MC_CTRL_PI = 1 } mc_ctrl_kind;
+typedef enum { MC_FP64 = 0, MC_MIXED = 1 } mc_precision;
+typedef enum {
+  MC_QP_ACTIVE_SET = 0,   /* Riccati-based primal active-set method          */
+  MC_QP_IPM = 1           /* Riccati-based primal-dual interior point (Mehrotra) */
+} mc_qp_solver;
+
+/* Plant, NMPC model and closed-loop set-up (Sec. VI, VII-A). */
+typedef struct {
+  double V, k0, EaR, beta, cA_in, cB_in, T_in; /* CSTR parameters, Eq. (CSTR)   */
+  double sigma[3];        /* diagonal of sigma-bar (mol/L, mol/L, K)           */
+  double meas_sd;         /* sqrt(R), measurement noise sd (K); > 0           */
+  double Ts, t0;          /* sample time and start time (s)                    */
+  int32_t n_steps;        /* control steps K (Phi has K+1 terms)               */
+  int32_t n_em;           /* Euler-Maruyama substeps per sample, N_s           */
+  int32_t n_setpoints;    /* 1..MC_MAX_SETPOINTS                               */
+  int32_t reserved0;
+  const double* sp_time;  /* host, n_setpoints: segment start times, ascending */
+  const double* sp_value; /* host, n_setpoints: set-point temperatures (K)     */
+  double Ea_logsd;        /* lognormal sd of E_a/R per trajectory, 0 = off     */
+  double dT_in_step;      /* +- step of T_in at a uniform random time, 0 = off */
+} mc_model_t;
+
+/* Controller (Sec. III-V, VII-A). */
+typedef struct {
+  int32_t kind;           /* mc_ctrl_kind                                      */
+  int32_t precision;      /* mc_precision                                      */
+  double u_min, u_max;    /* input bounds (mL/min)                             */
+  double kP, kI, kaw;     /* PI gains; act on F in L/s and e in K             */
+  int32_t N;              /* prediction horizon, 1..MC_MAX_HORIZON             */
+  int32_t n_rk4;          /* classical RK4 steps per interval, N_c             */
+  double Qz;              /* output weight of the NMPC objective               */
+  double P0;              /* initial EKF covariance P_{-1|-1} ((K L)^2)        */
+  int32_t sqp_max_it;     /* SQP iteration limit (a hit counts as failed OCP)  */
+  int32_t ls_max;         /* maximum step halvings of the line search          */
+  double sqp_tol;         /* epsilon of the scaled KKT test                    */
+  int32_t qp_solver;      /* mc_qp_solver                                      */
+  int32_t ip_max_it;      /* interior-point iteration limit                   */
+  double ip_tol;          /* interior-point residual/complementarity tolerance */
+  double u_scale;         /* OCP input unit (mL/min)                           */
+  double x_scale;         /* OCP state unit (K L); V makes it kelvin           */
+} mc_controller_t;
+
+/* Reduced results of the last run (Table II and Fig. 3 of Sec. VII). */
+typedef struct {
+  int64_t n_traj;         /* trajectories in the last run                      */
+  int64_t n_ocp;          /* OCPs solved (NMPC: n_traj * n_steps)              */
+  int64_t n_ocp_failed;   /* OCPs stopped by the SQP iteration limit           */
+  int64_t n_ls_fail;      /* OCPs stopped by a failed line search              */
+  int64_t n_hess_reset;   /* block-BFGS resets to the identity                 */
+  int64_t n_nonfinite;    /* trajectories whose state became non-finite        */
+  int64_t sqp_iters;      /* QP subproblems solved                             */
+  int64_t ls_trials;      /* merit evaluations in the line searches            */
+  int64_t qp_iters;       /* QP solver iterations (active-set or IPM)          */
+  int64_t qp_fail;        /* QP subproblems that hit their iteration limit     */
+  double phi_mean, phi_var, phi_min, phi_max; /* over finite trajectories      */
+  int32_t n_bins;         /* histogram of Phi                                  */
+  int32_t reserved0;
+  double bin_lo, bin_hi;
+  int64_t hist[MC_MAX_BINS];
+  double gpu_ms;          /* device time of the last mc_run (CUDA events)      */
+} mc_stats_t;
+
+typedef struct mc_handle mc_handle;
+
+/* Validate the configuration and allocate device buffers for n_sims
+ * trajectories (indices 0 .. n_sims-1).  Trajectory j draws its noise from
+ * Philox4x32-10 with key `seed` and counters carrying j, so handles with the
+ * same seed (an NMPC and a PI handle, say) see common random numbers, and any
+ * trajectory's result is independent of how runs are split.
+ * Returns MC_EINVAL (with the reason in mc_last_error(NULL)) or MC_ENOMEM. */
+mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl,
+                    int64_t n_sims, uint64_t seed, mc_handle** out);
+
+/* Histogram of Phi with n_bins (1..MC_MAX_BINS) equal bins on [lo, hi);
+ * lo >= hi selects the [min, max] of the run itself.  Values outside are
+ * counted in the first/last bin. */
+mc_status mc_set_histogram(mc_handle* h, int32_t n_bins, double lo, double hi);
+
+/* Simulate all trajectories (Sec. VII-C: Monte Carlo over process and
+ * measurement noise) and reduce the statistics, asynchronously on the stream. */
+mc_status mc_run(mc_handle* h, void* cuda_stream);
+
+/* Simulate trajectories j0 .. j1-1 only (0 <= j0 <= j1 <= n_sims) and reduce
+ * the statistics over that range.  Per-trajectory results of other indices
+ * are kept. */
+mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream);
+
+/* Wait for the last run (polling, at most timeout_ms; <= 0 waits without limit)
+ * and copy its statistics.  Returns MC_ETIMEOUT if the GPU has not finished,
+ * MC_WARN_NONFINITE if some trajectory became non-finite. */
+mc_status mc_stats(mc_handle* h, mc_stats_t* out, int64_t timeout_ms);
+
+/* Copy Phi of trajectories j0 .. j0+n-1 (after a run) to dst. */
+mc_status mc_copy_phi(mc_handle* h, int64_t j0, int64_t n, double* dst, int dst_is_device);
+
+/* Copy the per-trajectory counters of trajectories j0 .. j0+n-1, row-major
+ * n x MC_N_COUNTERS int32: [n_ocp_failed, sqp_iters, ls_trials, n_hess_reset,
+ * n_ls_fail, qp_iters, nonfinite, qp_fail]. */
+mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
+                           int dst_is_device);
+
+/* Block until all work of the handle's last run has finished (timeout as in
+ * mc_stats). */
+mc_status mc_sync(mc_handle* h, int64_t timeout_ms);
+
+void mc_destroy(mc_handle* h);
+const char* mc_status_str(mc_status s);
+/* last error message of a handle; NULL gives the last mc_create failure */
+const char* mc_last_error(const mc_handle* h);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks of the hot path, exposed for batched use and for testing
+ * each step against an independent implementation.  All pointers are host
+ * memory; the call copies in, runs one kernel and copies out (blocking).
+ * ------------------------------------------------------------------------- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) on n counters: ctr_host (n x 4),
+ * key (2 words), out_host (n x 4). */
+mc_status mc_philox(const uint32_t* ctr_host, const uint32_t key[2], int64_t n,
+                    uint32_t* out_host);
+
+/* The closed loop's noise for trajectory j, as the simulation draws it:
+ * process noise of substeps k0 .. k0+nk-1 (out_host, nk x 3 standard
+ * normals, Sec. II d-omega) and measurement noise of samples k0 .. k0+nk-1
+ * (meas_host, nk standard normals).  precision selects the FP64 or FP32
+ * transform of the same Philox words. */
+mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t precision,
+                   double* out_host, double* meas_host);
+
+/* Solve n structured QP subproblems, Eq. (QP-subproblem)/(nlpsqp_qp), with the
+ * selected solver.  Inputs are n x N (A, B, b, r, lb, ub) and n x (N+1)
+ * (Wxx, Wxu, Wuu, q) row-major host arrays (A[.,0], Wxx[.,0], Wxu[.,0],
+ * Wxu[.,N], Wuu[.,N], q[.,0] unused); outputs du, mu, nul, nuu (n x N),
+ * dx (n x (N+1)), iters and status (n; 0 = solved, 1 = iteration limit,
+ * 2 = not positive definite). */
+mc_status mc_qp_solve_batch(int32_t N, int64_t n, int32_t solver, int32_t max_it,
+                            double tol, const double* A, const double* B, const double* b,
+                            const double* Wxx, const double* Wxu, const double* Wuu,
+                            const double* q, const double* r, const double* lb,
+                            const double* ub, double* du, double* dx, double* mu,
+                            double* nul, double* nuu, int32_t* iters, int32_t* status);
+
+/* Solve n NMPC OCPs (Sec. III-B) by the SQP of Sec. IV from the given warm
+ * starts.  x0 (n): initial OCP states; EaR (n): activation energies;
+ * zbar (n x (N+1), column 0 unused): set-points z-bar(t_{i+k}); u (n x N),
+ * x (n x (N+1)), lam, pil, piu (n x N) are read as the warm start and
+ * overwritten with the solution; info (n x 4 int32): [iters, status
+ * (0 converged, 1 iteration limit, 2 line search), ls_trials, qp_iters];
+ * kkt (n x 3 double): [||grad L / s_d||_inf, ||g||_inf, f]. */
+mc_status mc_ocp_solve_batch(const mc_model_t* model, const mc_controller_t* ctrl,
+                             int64_t n, const double* x0, const double* EaR,
+                             const double* zbar, double* u, double* x, double* lam,
+                             double* pil, double* piu, int32_t* info, double* kkt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

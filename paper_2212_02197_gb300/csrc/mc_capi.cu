@@ -1,0 +1,799 @@
+// mc_capi.cu -- kernels and the C ABI declared in include/mc.h.
+//
+// Kernels:
+//   k_nmpc       one thread per NMPC trajectory (grid-stride over trajectories),
+//                per-thread arrays in a structure-of-arrays scratch buffer
+//   k_pi         one thread per PI trajectory, registers only
+//   k_stats_*    reduction of Phi and of the per-trajectory counters: block
+//                partials (count/mean/M2 merged by Chan's formula, min, max,
+//                counter sums) then one block merging them and binning Phi
+//   k_philox, k_noise, k_qp_batch, k_ocp_batch   building blocks on their own
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mc.h"
+#include "mc_closedloop.cuh"
+
+namespace mc {
+
+// --------------------------------------------------------------- kernels
+
+__global__ void __launch_bounds__(128) k_nmpc(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
+                                              double* __restrict__ phi,
+                                              int32_t* __restrict__ cnt, double* ws,
+                                              int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ld) return;
+  const Ws w{ws + t, ld, c.N + 1};
+  for (int64_t j = j0 + t; j < j1; j += ld) {
+    const TrajOut o = traj_nmpc(m, c, (uint32_t)j, w);
+    phi[j] = o.phi;
+#pragma unroll
+    for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_pi(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
+                                            double* __restrict__ phi,
+                                            int32_t* __restrict__ cnt) {
+  const int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= j1) return;
+  const TrajOut o = traj_pi<R>(m, c, (uint32_t)j);
+  phi[j] = o.phi;
+#pragma unroll
+  for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
+}
+
+struct Partial {
+  double n, mean, m2, mn, mx;
+  long long sums[kNCounters];
+  long long n_nonfinite;
+};
+
+// Chan et al. merge of (count, mean, M2).
+__device__ __forceinline__ void chan_merge(double& n, double& mean, double& m2, double nb,
+                                           double meanb, double m2b) {
+  if (nb == 0.0) return;
+  if (n == 0.0) {
+    n = nb;
+    mean = meanb;
+    m2 = m2b;
+    return;
+  }
+  const double nt = n + nb;
+  const double d = meanb - mean;
+  mean = mean + d * (nb / nt);
+  m2 = m2 + m2b + d * d * (n * nb / nt);
+  n = nt;
+}
+
+constexpr int kStatThreads = 256;
+
+__device__ void block_reduce_partial(Partial& p) {
+  __shared__ double sh[kStatThreads / 32][5];
+  __shared__ long long shc[kStatThreads / 32][kNCounters + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double nb = __shfl_down_sync(0xffffffffu, p.n, off);
+    const double mb = __shfl_down_sync(0xffffffffu, p.mean, off);
+    const double qb = __shfl_down_sync(0xffffffffu, p.m2, off);
+    const double mnb = __shfl_down_sync(0xffffffffu, p.mn, off);
+    const double mxb = __shfl_down_sync(0xffffffffu, p.mx, off);
+    chan_merge(p.n, p.mean, p.m2, nb, mb, qb);
+    p.mn = fmin(p.mn, mnb);
+    p.mx = fmax(p.mx, mxb);
+    for (int q = 0; q < kNCounters; ++q) p.sums[q] += __shfl_down_sync(0xffffffffu, p.sums[q], off);
+    p.n_nonfinite += __shfl_down_sync(0xffffffffu, p.n_nonfinite, off);
+  }
+  if (lane == 0) {
+    sh[wid][0] = p.n; sh[wid][1] = p.mean; sh[wid][2] = p.m2; sh[wid][3] = p.mn; sh[wid][4] = p.mx;
+    for (int q = 0; q < kNCounters; ++q) shc[wid][q] = p.sums[q];
+    shc[wid][kNCounters] = p.n_nonfinite;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int v = 1; v < kStatThreads / 32; ++v) {
+      chan_merge(p.n, p.mean, p.m2, sh[v][0], sh[v][1], sh[v][2]);
+      p.mn = fmin(p.mn, sh[v][3]);
+      p.mx = fmax(p.mx, sh[v][4]);
+      for (int q = 0; q < kNCounters; ++q) p.sums[q] += shc[v][q];
+      p.n_nonfinite += shc[v][kNCounters];
+    }
+  }
+}
+
+__device__ __forceinline__ Partial empty_partial() {
+  Partial p;
+  p.n = 0.0; p.mean = 0.0; p.m2 = 0.0; p.mn = INFINITY; p.mx = -INFINITY;
+  for (int q = 0; q < kNCounters; ++q) p.sums[q] = 0;
+  p.n_nonfinite = 0;
+  return p;
+}
+
+// Block partials over trajectories j0 .. j1-1 (grid-stride).
+__global__ void __launch_bounds__(kStatThreads) k_stats_partial(const double* __restrict__ phi,
+                                                                 const int32_t* __restrict__ cnt,
+                                                                 int64_t j0, int64_t j1,
+                                                                 Partial* __restrict__ part) {
+  Partial p = empty_partial();
+  for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < j1;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double v = phi[j];
+    if (isfinite(v)) {
+      chan_merge(p.n, p.mean, p.m2, 1.0, v, 0.0);
+      p.mn = fmin(p.mn, v);
+      p.mx = fmax(p.mx, v);
+    } else {
+      p.n_nonfinite++;
+    }
+    for (int q = 0; q < kNCounters; ++q) p.sums[q] += cnt[j * kNCounters + q];
+  }
+  block_reduce_partial(p);
+  if (threadIdx.x == 0) part[blockIdx.x] = p;
+}
+
+struct DevStats {
+  double n, mean, m2, mn, mx, lo, hi;
+  long long sums[kNCounters];
+  long long n_nonfinite;
+  long long hist[MC_MAX_BINS];
+};
+
+// One block: merge the partials, fix the histogram range, bin Phi.
+__global__ void __launch_bounds__(kStatThreads) k_stats_final(const Partial* __restrict__ part,
+                                                               int nparts,
+                                                               const double* __restrict__ phi,
+                                                               int64_t j0, int64_t j1, int n_bins,
+                                                               double lo, double hi,
+                                                               DevStats* __restrict__ out) {
+  __shared__ unsigned long long hist[MC_MAX_BINS];
+  __shared__ double range[2];
+  Partial p = empty_partial();
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    const Partial& q = part[b];
+    chan_merge(p.n, p.mean, p.m2, q.n, q.mean, q.m2);
+    p.mn = fmin(p.mn, q.mn);
+    p.mx = fmax(p.mx, q.mx);
+    for (int k = 0; k < kNCounters; ++k) p.sums[k] += q.sums[k];
+    p.n_nonfinite += q.n_nonfinite;
+  }
+  for (int b = threadIdx.x; b < MC_MAX_BINS; b += blockDim.x) hist[b] = 0ull;
+  block_reduce_partial(p);
+  if (threadIdx.x == 0) {
+    double l = lo, h = hi;
+    if (!(l < h)) {
+      l = p.mn;
+      h = p.mx;
+      if (!(l < h)) h = l + 1.0;
+    }
+    range[0] = l;
+    range[1] = h;
+    out->n = p.n; out->mean = p.mean; out->m2 = p.m2; out->mn = p.mn; out->mx = p.mx;
+    out->lo = l; out->hi = h;
+    for (int k = 0; k < kNCounters; ++k) out->sums[k] = p.sums[k];
+    out->n_nonfinite = p.n_nonfinite;
+  }
+  __syncthreads();
+  const double l = range[0], scale = (double)n_bins / (range[1] - range[0]);
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const double v = phi[j];
+    if (!isfinite(v)) continue;
+    int b = (int)floor((v - l) * scale);
+    b = b < 0 ? 0 : (b >= n_bins ? n_bins - 1 : b);
+    atomicAdd(&hist[b], 1ull);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < MC_MAX_BINS; b += blockDim.x)
+    out->hist[b] = (b < n_bins) ? (long long)hist[b] : 0;
+}
+
+__global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1, int64_t n,
+                         uint4* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void k_noise(DevModel m, uint32_t j, int64_t k0, int64_t nk, int precision,
+                        double* __restrict__ out, double* __restrict__ meas) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk) return;
+  const uint32_t k = (uint32_t)(k0 + i);
+  if (precision == 0) {
+    double xi[3];
+    process_noise<double>(m, j, k, xi);
+    out[3 * i] = xi[0]; out[3 * i + 1] = xi[1]; out[3 * i + 2] = xi[2];
+    meas[i] = meas_noise<double>(m, j, k);
+  } else {
+    float xi[3];
+    process_noise<float>(m, j, k, xi);
+    out[3 * i] = xi[0]; out[3 * i + 1] = xi[1]; out[3 * i + 2] = xi[2];
+    meas[i] = meas_noise<float>(m, j, k);
+  }
+}
+
+struct QpBatch {
+  const double *A, *B, *b, *Wxx, *Wxu, *Wuu, *q, *r, *lb, *ub;
+  double *du, *dx, *mu, *nul, *nuu;
+  int32_t *iters, *status;
+};
+
+__global__ void k_qp_batch(int N, int64_t n, int solver, int max_it, double tol, QpBatch d,
+                           double* ws, int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const Ws w{ws + t, ld, N + 1};
+  const int64_t o1 = t * N, o2 = t * (N + 1);
+  for (int k = 0; k < N; ++k) {
+    w(EA, k) = d.A[o1 + k];
+    w(EB, k) = d.B[o1 + k];
+    w(EG, k) = d.b[o1 + k];
+    w(QR, k) = d.r[o1 + k];
+    w(LB, k) = d.lb[o1 + k];
+    w(UB, k) = d.ub[o1 + k];
+  }
+  for (int k = 0; k <= N; ++k) {
+    w(WXX, k) = d.Wxx[o2 + k];
+    w(WXU, k) = d.Wxu[o2 + k];
+    w(WUU, k) = d.Wuu[o2 + k];
+    w(EQ, k) = d.q[o2 + k];
+  }
+  const QpResult r = (solver == MC_QP_IPM) ? qp_ipm(w, N, true, max_it, tol)
+                                            : qp_active_set(w, N, true, max_it);
+  for (int k = 0; k < N; ++k) {
+    d.du[o1 + k] = w(DU, k);
+    d.mu[o1 + k] = w(MU, k);
+    d.nul[o1 + k] = w(NUL, k);
+    d.nuu[o1 + k] = w(NUU, k);
+  }
+  d.dx[o2] = 0.0;
+  for (int k = 1; k <= N; ++k) d.dx[o2 + k] = w(DX, k);
+  d.iters[t] = r.iters;
+  d.status[t] = r.status;
+}
+
+struct OcpBatch {
+  const double *x0, *EaR, *zbar;
+  double *u, *x, *lam, *pil, *piu, *kkt;
+  int32_t* info;
+};
+
+__global__ void k_ocp_batch(DevModel m, DevCtrl c, int64_t n, OcpBatch d, double* ws,
+                            int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int N = c.N;
+  const Ws w{ws + t, ld, N + 1};
+  const int64_t o1 = t * N, o2 = t * (N + 1);
+  for (int k = 0; k < N; ++k) {
+    w(U, k) = d.u[o1 + k];
+    w(LAM, k) = d.lam[o1 + k];
+    w(PIL, k) = d.pil[o1 + k];
+    w(PIU, k) = d.piu[o1 + k];
+  }
+  for (int k = 0; k <= N; ++k) {
+    w(X, k) = d.x[o2 + k];
+    w(ZB, k) = d.zbar[o2 + k];
+  }
+  const SqpInfo si = sqp_solve(m, c, d.EaR[t], d.x0[t], w);
+  for (int k = 0; k < N; ++k) {
+    d.u[o1 + k] = w(U, k);
+    d.lam[o1 + k] = w(LAM, k);
+    d.pil[o1 + k] = w(PIL, k);
+    d.piu[o1 + k] = w(PIU, k);
+  }
+  for (int k = 0; k <= N; ++k) d.x[o2 + k] = w(X, k);
+  d.info[4 * t + 0] = si.iters;
+  d.info[4 * t + 1] = si.status;
+  d.info[4 * t + 2] = si.ls_trials;
+  d.info[4 * t + 3] = si.qp_iters;
+  d.kkt[3 * t + 0] = si.kkt_grad;
+  d.kkt[3 * t + 1] = si.kkt_eq;
+  d.kkt[3 * t + 2] = si.f;
+}
+
+}  // namespace mc
+
+// =========================================================================
+// host side
+// =========================================================================
+
+using namespace mc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kNmpcThreads = 128;
+constexpr int kMaxStatBlocks = 1024;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mc_handle {
+  DevModel m;
+  DevCtrl c;
+  int64_t n_sims = 0;
+  int n_bins = 64;
+  double bin_lo = 0.0, bin_hi = 0.0;
+  double* phi = nullptr;       // n_sims
+  int32_t* cnt = nullptr;      // n_sims x kNCounters
+  double* ws = nullptr;        // NMPC scratch: kNArr * (N+1) x ws_ld
+  int64_t ws_ld = 0;
+  Partial* part = nullptr;     // kMaxStatBlocks
+  DevStats* dstats = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool ran = false;
+  int64_t last_j0 = 0, last_j1 = 0;
+  std::string err;
+};
+
+static mc_status fail(mc_handle* h, mc_status s, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+static mc_status cuda_fail(mc_handle* h, cudaError_t e, const char* what) {
+  return fail(h, MC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MC_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint64_t seed,
+                          DevModel* m, DevCtrl* c, std::string* why) {
+  auto bad = [&](const char* s) {
+    *why = s;
+    return MC_EINVAL;
+  };
+  if (!mm || !cc) return bad("null model or controller");
+  if (!(mm->V > 0) || !(mm->beta > 0) || !(mm->k0 >= 0) || !(mm->EaR > 0))
+    return bad("CSTR parameters must be positive (V, beta, EaR > 0, k0 >= 0)");
+  if (!(mm->Ts > 0) || mm->n_em < 1 || mm->n_steps < 0)
+    return bad("need Ts > 0, n_em >= 1, n_steps >= 0");
+  if (mm->n_setpoints < 1 || mm->n_setpoints > MC_MAX_SETPOINTS || !mm->sp_time || !mm->sp_value)
+    return bad("need 1..16 set-point segments with time and value arrays");
+  if (!(mm->meas_sd >= 0) || !(mm->sigma[0] >= 0) || !(mm->sigma[1] >= 0) || !(mm->sigma[2] >= 0))
+    return bad("noise intensities must be non-negative");
+  if ((int64_t)mm->n_steps * mm->n_em >= (int64_t)1 << 32)
+    return bad("n_steps * n_em must stay below 2^32 (Philox counter word)");
+  if (cc->kind != MC_CTRL_NMPC && cc->kind != MC_CTRL_PI) return bad("unknown controller kind");
+  if (cc->precision != MC_FP64 && cc->precision != MC_MIXED) return bad("unknown precision");
+  if (!(cc->u_min <= cc->u_max)) return bad("need u_min <= u_max");
+  if (cc->kind == MC_CTRL_NMPC) {
+    if (cc->N < 1 || cc->N > MC_MAX_HORIZON) return bad("NMPC horizon N must be in 1..64");
+    if (cc->n_rk4 < 1) return bad("n_rk4 must be >= 1");
+    if (cc->sqp_max_it < 0 || cc->ls_max < 0) return bad("iteration limits must be >= 0");
+    if (!(cc->sqp_tol > 0)) return bad("sqp_tol must be > 0");
+    if (!(mm->meas_sd > 0)) return bad("the CD-EKF needs a measurement noise sd > 0");
+    if (!(cc->u_scale > 0) || !(cc->x_scale > 0)) return bad("u_scale and x_scale must be > 0");
+    if (cc->qp_solver != MC_QP_ACTIVE_SET && cc->qp_solver != MC_QP_IPM)
+      return bad("unknown QP solver");
+    if (cc->qp_solver == MC_QP_IPM && (cc->ip_max_it < 1 || !(cc->ip_tol > 0)))
+      return bad("the interior-point solver needs ip_max_it >= 1 and ip_tol > 0");
+    if (cc->precision == MC_MIXED) return bad("mixed precision is available for PI only");
+  }
+  memset(m, 0, sizeof(*m));
+  m->V = mm->V; m->k0 = mm->k0; m->EaR = mm->EaR; m->beta = mm->beta;
+  m->cA_in = mm->cA_in; m->cB_in = mm->cB_in; m->T_in = mm->T_in;
+  for (int i = 0; i < 3; ++i) m->sigma[i] = mm->sigma[i];
+  m->meas_sd = mm->meas_sd; m->Ts = mm->Ts; m->t0 = mm->t0;
+  m->n_steps = mm->n_steps; m->n_em = mm->n_em; m->n_sp = mm->n_setpoints;
+  for (int s = 0; s < mm->n_setpoints; ++s) {
+    m->sp_time[s] = mm->sp_time[s];
+    m->sp_value[s] = mm->sp_value[s];
+    if (s > 0 && !(mm->sp_time[s] > mm->sp_time[s - 1]))
+      return bad("set-point times must increase");
+  }
+  m->Ea_logsd = mm->Ea_logsd; m->dTin = mm->dT_in_step;
+  m->iV = 1.0 / mm->V; m->ib = 1.0 / mm->beta;
+  m->key0 = (uint32_t)seed; m->key1 = (uint32_t)(seed >> 32);
+  memset(c, 0, sizeof(*c));
+  c->kind = cc->kind; c->precision = cc->precision; c->N = cc->N; c->n_rk4 = cc->n_rk4;
+  c->sqp_max_it = cc->sqp_max_it; c->ls_max = cc->ls_max; c->qp_solver = cc->qp_solver;
+  c->ip_max_it = cc->ip_max_it;
+  c->u_min = cc->u_min; c->u_max = cc->u_max; c->kP = cc->kP; c->kI = cc->kI; c->kaw = cc->kaw;
+  c->Qz = cc->Qz; c->P0 = cc->P0; c->sqp_tol = cc->sqp_tol; c->ip_tol = cc->ip_tol;
+  c->u_scale = cc->u_scale; c->x_scale = cc->x_scale;
+  if (cc->kind == MC_CTRL_NMPC) {
+    c->Fconv = cc->u_scale / 60000.0;
+    c->vmin = cc->u_min / cc->u_scale;
+    c->vmax = cc->u_max / cc->u_scale;
+  }
+  return MC_OK;
+}
+
+template <class T>
+static bool to_dev(T** d, const T* h, size_t n) {
+  if (cudaMalloc((void**)d, sizeof(T) * (n ? n : 1)) != cudaSuccess) return false;
+  if (n && h && cudaMemcpy(*d, h, sizeof(T) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  return true;
+}
+
+static int64_t nmpc_threads_for(int64_t n) {
+  // every trajectory gets its own thread while they fit on the GPU at once
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nmpc, kNmpcThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 4;
+  const int64_t cap = (int64_t)sms * per_sm * kNmpcThreads;
+  int64_t t = n < cap ? n : cap;
+  t = (t + kNmpcThreads - 1) / kNmpcThreads * kNmpcThreads;
+  return t < kNmpcThreads ? kNmpcThreads : t;
+}
+
+extern "C" {
+
+const char* mc_status_str(mc_status s) {
+  switch (s) {
+    case MC_OK: return "ok";
+    case MC_EINVAL: return "invalid argument";
+    case MC_ENOMEM: return "out of device memory";
+    case MC_ECUDA: return "CUDA error";
+    case MC_ETIMEOUT: return "timed out waiting for the GPU";
+    case MC_ENOTRUN: return "no run yet";
+    case MC_WARN_NONFINITE: return "some trajectories became non-finite";
+  }
+  return "unknown status";
+}
+
+const char* mc_last_error(const mc_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void mc_destroy(mc_handle* h) {
+  if (!h) return;
+  cudaFree(h->phi);
+  cudaFree(h->cnt);
+  cudaFree(h->ws);
+  cudaFree(h->part);
+  cudaFree(h->dstats);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl, int64_t n_sims,
+                    uint64_t seed, mc_handle** out) {
+  if (!out) return fail(nullptr, MC_EINVAL, "out is null");
+  *out = nullptr;
+  if (n_sims < 0 || n_sims > ((int64_t)1 << 32))
+    return fail(nullptr, MC_EINVAL, "n_sims must be in 0..2^32");
+  auto* h = new mc_handle();
+  std::string why;
+  if (fill_dev(model, ctrl, seed, &h->m, &h->c, &why) != MC_OK) {
+    delete h;
+    return fail(nullptr, MC_EINVAL, why);
+  }
+  h->n_sims = n_sims;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (bytes == 0) bytes = 8;
+    return cudaMalloc(p, bytes) == cudaSuccess;
+  };
+  bool ok = alloc((void**)&h->phi, sizeof(double) * n_sims) &&
+            alloc((void**)&h->cnt, sizeof(int32_t) * kNCounters * n_sims) &&
+            alloc((void**)&h->part, sizeof(Partial) * kMaxStatBlocks) &&
+            alloc((void**)&h->dstats, sizeof(DevStats));
+  if (ok && h->c.kind == MC_CTRL_NMPC && n_sims > 0) {
+    h->ws_ld = nmpc_threads_for(n_sims);
+    const size_t words = (size_t)kNArr * (h->c.N + 1) * (size_t)h->ws_ld;
+    ok = alloc((void**)&h->ws, words * sizeof(double));
+  }
+  if (!ok) {
+    cudaGetLastError();
+    mc_destroy(h);
+    return fail(nullptr, MC_ENOMEM, "cudaMalloc failed for the trajectory buffers");
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    mc_destroy(h);
+    return fail(nullptr, MC_ECUDA, "cudaEventCreate failed");
+  }
+  *out = h;
+  return MC_OK;
+}
+
+mc_status mc_set_histogram(mc_handle* h, int32_t n_bins, double lo, double hi) {
+  if (!h) return MC_EINVAL;
+  if (n_bins < 1 || n_bins > MC_MAX_BINS) return fail(h, MC_EINVAL, "n_bins must be 1..256");
+  h->n_bins = n_bins;
+  h->bin_lo = lo;
+  h->bin_hi = hi;
+  return MC_OK;
+}
+
+static mc_status launch_stats(mc_handle* h, int64_t j0, int64_t j1, cudaStream_t st) {
+  const int64_t n = j1 - j0;
+  int nb = (int)((n + kStatThreads - 1) / kStatThreads);
+  nb = nb < 1 ? 1 : (nb > kMaxStatBlocks ? kMaxStatBlocks : nb);
+  k_stats_partial<<<nb, kStatThreads, 0, st>>>(h->phi, h->cnt, j0, j1, h->part);
+  k_stats_final<<<1, kStatThreads, 0, st>>>(h->part, nb, h->phi, j0, j1, h->n_bins, h->bin_lo,
+                                            h->bin_hi, h->dstats);
+  MC_CUDA(h, cudaGetLastError());
+  return MC_OK;
+}
+
+mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) {
+  if (!h) return MC_EINVAL;
+  if (j0 < 0 || j1 < j0 || j1 > h->n_sims) return fail(h, MC_EINVAL, "bad trajectory range");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  MC_CUDA(h, cudaEventRecord(h->ev0, st));
+  if (j1 > j0) {
+    if (h->c.kind == MC_CTRL_NMPC) {
+      const int64_t n = j1 - j0;
+      int64_t threads = n < h->ws_ld ? n : h->ws_ld;
+      const int64_t blocks = (threads + kNmpcThreads - 1) / kNmpcThreads;
+      // the scratch stride is the allocation's, the thread count the range's
+      k_nmpc<<<(unsigned)blocks, kNmpcThreads, 0, st>>>(h->m, h->c, j0, j1, h->phi, h->cnt,
+                                                        h->ws, h->ws_ld);
+    } else {
+      const int64_t blocks = (j1 - j0 + 127) / 128;
+      if (h->c.precision == MC_FP64)
+        k_pi<double><<<(unsigned)blocks, 128, 0, st>>>(h->m, h->c, j0, j1, h->phi, h->cnt);
+      else
+        k_pi<float><<<(unsigned)blocks, 128, 0, st>>>(h->m, h->c, j0, j1, h->phi, h->cnt);
+    }
+    MC_CUDA(h, cudaGetLastError());
+  }
+  mc_status s = launch_stats(h, j0, j1, st);
+  if (s != MC_OK) return s;
+  MC_CUDA(h, cudaEventRecord(h->ev1, st));
+  h->ran = true;
+  h->last_j0 = j0;
+  h->last_j1 = j1;
+  return MC_OK;
+}
+
+mc_status mc_run(mc_handle* h, void* cuda_stream) {
+  if (!h) return MC_EINVAL;
+  return mc_run_range(h, 0, h->n_sims, cuda_stream);
+}
+
+mc_status mc_sync(mc_handle* h, int64_t timeout_ms) {
+  if (!h) return MC_EINVAL;
+  if (!h->ran) return fail(h, MC_ENOTRUN, "mc_run has not been called");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(h->ev1);
+    if (e == cudaSuccess) return MC_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(h, e, "waiting for the run");
+    if (timeout_ms > 0) {
+      const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+      if (ms > timeout_ms) return fail(h, MC_ETIMEOUT, "the run did not finish in time");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+}
+
+mc_status mc_stats(mc_handle* h, mc_stats_t* out, int64_t timeout_ms) {
+  if (!h || !out) return MC_EINVAL;
+  mc_status s = mc_sync(h, timeout_ms);
+  if (s != MC_OK) return s;
+  DevStats d;
+  MC_CUDA(h, cudaMemcpy(&d, h->dstats, sizeof(d), cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  const int64_t n = h->last_j1 - h->last_j0;
+  out->n_traj = n;
+  out->n_ocp = (h->c.kind == MC_CTRL_NMPC) ? n * (int64_t)h->m.n_steps : 0;
+  out->n_ocp_failed = d.sums[0];
+  out->sqp_iters = d.sums[1];
+  out->ls_trials = d.sums[2];
+  out->n_hess_reset = d.sums[3];
+  out->n_ls_fail = d.sums[4];
+  out->qp_iters = d.sums[5];
+  out->n_nonfinite = d.n_nonfinite;
+  out->qp_fail = d.sums[7];
+  out->phi_mean = d.mean;
+  out->phi_var = (d.n > 1) ? d.m2 / (d.n - 1.0) : 0.0;
+  out->phi_min = d.mn;
+  out->phi_max = d.mx;
+  out->n_bins = h->n_bins;
+  out->bin_lo = d.lo;
+  out->bin_hi = d.hi;
+  for (int b = 0; b < MC_MAX_BINS; ++b) out->hist[b] = d.hist[b];
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) out->gpu_ms = ms;
+  return d.n_nonfinite > 0 ? MC_WARN_NONFINITE : MC_OK;
+}
+
+mc_status mc_copy_phi(mc_handle* h, int64_t j0, int64_t n, double* dst, int dst_is_device) {
+  if (!h || (!dst && n > 0)) return MC_EINVAL;
+  if (j0 < 0 || n < 0 || j0 + n > h->n_sims) return fail(h, MC_EINVAL, "bad range");
+  if (n == 0) return MC_OK;
+  mc_status s = mc_sync(h, 0);
+  if (s != MC_OK) return s;
+  MC_CUDA(h, cudaMemcpy(dst, h->phi + j0, sizeof(double) * n,
+                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
+mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
+                           int dst_is_device) {
+  if (!h || (!dst && n > 0)) return MC_EINVAL;
+  if (j0 < 0 || n < 0 || j0 + n > h->n_sims) return fail(h, MC_EINVAL, "bad range");
+  if (n == 0) return MC_OK;
+  mc_status s = mc_sync(h, 0);
+  if (s != MC_OK) return s;
+  MC_CUDA(h, cudaMemcpy(dst, h->cnt + j0 * kNCounters, sizeof(int32_t) * kNCounters * n,
+                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
+// ----------------------------------------------------------- building blocks
+
+mc_status mc_philox(const uint32_t* ctr_host, const uint32_t key[2], int64_t n,
+                    uint32_t* out_host) {
+  if (n < 0 || (n > 0 && (!ctr_host || !out_host || !key)))
+    return fail(nullptr, MC_EINVAL, "mc_philox: bad arguments");
+  if (n == 0) return MC_OK;
+  uint4 *dc = nullptr, *dout = nullptr;
+  mc_status s = MC_OK;
+  if (!to_dev(&dc, (const uint4*)ctr_host, n) || !to_dev<uint4>(&dout, nullptr, n)) {
+    s = fail(nullptr, MC_ENOMEM, "mc_philox: allocation");
+  } else {
+    k_philox<<<(unsigned)((n + 255) / 256), 256>>>(dc, key[0], key[1], n, dout);
+    cudaError_t e = cudaMemcpy(out_host, dout, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_philox");
+  }
+  cudaFree(dc);
+  cudaFree(dout);
+  return s;
+}
+
+mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t precision,
+                   double* out_host, double* meas_host) {
+  if (nk < 0 || j < 0 || k0 < 0 || (nk > 0 && (!out_host || !meas_host)))
+    return fail(nullptr, MC_EINVAL, "mc_noise: bad arguments");
+  if (nk == 0) return MC_OK;
+  DevModel m;
+  memset(&m, 0, sizeof(m));
+  m.key0 = (uint32_t)seed;
+  m.key1 = (uint32_t)(seed >> 32);
+  double *d = nullptr, *dm = nullptr;
+  mc_status s = MC_OK;
+  if (!to_dev<double>(&d, nullptr, 3 * nk) || !to_dev<double>(&dm, nullptr, nk)) {
+    s = fail(nullptr, MC_ENOMEM, "mc_noise: allocation");
+  } else {
+    k_noise<<<(unsigned)((nk + 127) / 128), 128>>>(m, (uint32_t)j, k0, nk, precision, d, dm);
+    cudaError_t e = cudaMemcpy(out_host, d, sizeof(double) * 3 * nk, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(meas_host, dm, sizeof(double) * nk, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_noise");
+  }
+  cudaFree(d);
+  cudaFree(dm);
+  return s;
+}
+
+mc_status mc_qp_solve_batch(int32_t N, int64_t n, int32_t solver, int32_t max_it, double tol,
+                            const double* A, const double* B, const double* b,
+                            const double* Wxx, const double* Wxu, const double* Wuu,
+                            const double* q, const double* r, const double* lb,
+                            const double* ub, double* du, double* dx, double* mu, double* nul,
+                            double* nuu, int32_t* iters, int32_t* status) {
+  if (N < 1 || N > MC_MAX_HORIZON || n < 0 || max_it < 1)
+    return fail(nullptr, MC_EINVAL, "mc_qp_solve_batch: bad sizes");
+  if (n == 0) return MC_OK;
+  const size_t n1 = (size_t)n * N, n2 = (size_t)n * (N + 1);
+  QpBatch d{};
+  std::vector<void*> owned;
+  bool ok = true;
+  auto up = [&](const double** dst, const double* src, size_t cnt) {
+    double* p = nullptr;
+    ok = ok && to_dev(&p, src, cnt);
+    owned.push_back(p);
+    *dst = p;
+  };
+  auto mk = [&](double** dst, size_t cnt) {
+    double* p = nullptr;
+    ok = ok && to_dev<double>(&p, nullptr, cnt);
+    owned.push_back(p);
+    *dst = p;
+  };
+  up(&d.A, A, n1); up(&d.B, B, n1); up(&d.b, b, n1); up(&d.r, r, n1);
+  up(&d.lb, lb, n1); up(&d.ub, ub, n1);
+  up(&d.Wxx, Wxx, n2); up(&d.Wxu, Wxu, n2); up(&d.Wuu, Wuu, n2); up(&d.q, q, n2);
+  mk(&d.du, n1); mk(&d.mu, n1); mk(&d.nul, n1); mk(&d.nuu, n1); mk(&d.dx, n2);
+  int32_t *di = nullptr, *ds = nullptr;
+  ok = ok && to_dev<int32_t>(&di, nullptr, n) && to_dev<int32_t>(&ds, nullptr, n);
+  owned.push_back(di);
+  owned.push_back(ds);
+  d.iters = di;
+  d.status = ds;
+  double* ws = nullptr;
+  const int64_t ld = n;
+  ok = ok && to_dev<double>(&ws, nullptr, (size_t)kNArr * (N + 1) * ld);
+  owned.push_back(ws);
+  mc_status s = MC_OK;
+  if (!ok) {
+    s = fail(nullptr, MC_ENOMEM, "mc_qp_solve_batch: allocation");
+  } else {
+    k_qp_batch<<<(unsigned)((n + 127) / 128), 128>>>(N, n, solver, max_it, tol, d, ws, ld);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(du, d.du, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(mu, d.mu, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(nul, d.nul, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(nuu, d.nuu, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dx, d.dx, sizeof(double) * n2, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(iters, di, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(status, ds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_qp_solve_batch");
+  }
+  for (void* p : owned) cudaFree(p);
+  return s;
+}
+
+mc_status mc_ocp_solve_batch(const mc_model_t* model, const mc_controller_t* ctrl, int64_t n,
+                             const double* x0, const double* EaR, const double* zbar,
+                             double* u, double* x, double* lam, double* pil, double* piu,
+                             int32_t* info, double* kkt) {
+  DevModel m;
+  DevCtrl c;
+  std::string why;
+  if (fill_dev(model, ctrl, 0, &m, &c, &why) != MC_OK)
+    return fail(nullptr, MC_EINVAL, "mc_ocp_solve_batch: " + why);
+  if (c.kind != MC_CTRL_NMPC) return fail(nullptr, MC_EINVAL, "mc_ocp_solve_batch: NMPC only");
+  if (n < 0) return fail(nullptr, MC_EINVAL, "mc_ocp_solve_batch: n < 0");
+  if (n == 0) return MC_OK;
+  const int N = c.N;
+  const size_t n1 = (size_t)n * N, n2 = (size_t)n * (N + 1);
+  OcpBatch d{};
+  std::vector<void*> owned;
+  bool ok = true;
+  auto up = [&](double** dst, const double* src, size_t cnt) {
+    double* p = nullptr;
+    ok = ok && to_dev(&p, src, cnt);
+    owned.push_back(p);
+    *dst = p;
+  };
+  double *dx0, *dEaR, *dzb;
+  up(&dx0, x0, n); up(&dEaR, EaR, n); up(&dzb, zbar, n2);
+  d.x0 = dx0; d.EaR = dEaR; d.zbar = dzb;
+  up(&d.u, u, n1); up(&d.x, x, n2); up(&d.lam, lam, n1); up(&d.pil, pil, n1);
+  up(&d.piu, piu, n1); up(&d.kkt, nullptr, 3 * n);
+  int32_t* di = nullptr;
+  ok = ok && to_dev<int32_t>(&di, nullptr, 4 * n);
+  owned.push_back(di);
+  d.info = di;
+  double* ws = nullptr;
+  ok = ok && to_dev<double>(&ws, nullptr, (size_t)kNArr * (N + 1) * n);
+  owned.push_back(ws);
+  mc_status s = MC_OK;
+  if (!ok) {
+    s = fail(nullptr, MC_ENOMEM, "mc_ocp_solve_batch: allocation");
+  } else {
+    k_ocp_batch<<<(unsigned)((n + 127) / 128), 128>>>(m, c, n, d, ws, n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(u, d.u, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(x, d.x, sizeof(double) * n2, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lam, d.lam, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(pil, d.pil, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(piu, d.piu, sizeof(double) * n1, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(info, di, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(kkt, d.kkt, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_ocp_solve_batch");
+  }
+  for (void* p : owned) cudaFree(p);
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,278 @@
+// mc_device.cuh -- device building blocks of the closed-loop Monte Carlo path:
+// counter-based noise, the CSTR model, Euler-Maruyama, RK4 shooting with
+// forward sensitivities, the CD-EKF and the PI law.
+//
+// Everything is per thread: one thread owns one trajectory (SIMT across
+// trajectories), so every FP64 instruction a warp issues does useful work for
+// 32 trajectories at once.  Functions are templated on the arithmetic type R
+// where the mixed-precision path runs them in FP32.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+// the QP/SQP building blocks are plain arithmetic and also compile for the host
+#define MC_HD __host__ __device__ __forceinline__
+
+namespace mc {
+
+constexpr int kMaxSp = 16;
+constexpr int kMaxN = 64;
+constexpr int kNCounters = 8;
+
+// Plant/model/closed-loop parameters as passed by value to every kernel.
+struct DevModel {
+  double V, k0, EaR, beta, cA_in, cB_in, T_in;
+  double sigma[3];
+  double meas_sd;
+  double Ts, t0;
+  int n_steps, n_em, n_sp, pad0;
+  double sp_time[kMaxSp], sp_value[kMaxSp];
+  double Ea_logsd, dTin;
+  double iV, ib;       // 1/V and 1/beta
+  uint32_t key0, key1;
+};
+
+struct DevCtrl {
+  int kind, precision, N, n_rk4;
+  int sqp_max_it, ls_max, qp_solver, ip_max_it;
+  double u_min, u_max, kP, kI, kaw, Qz, P0, sqp_tol, ip_tol, u_scale, x_scale;
+  double Fconv;        // OCP input unit -> L/s
+  double vmin, vmax;   // input bounds in OCP units
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit products whose high halves are xored with the other counter
+// words and the round key; the key advances by two Weyl constants per round.
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Open-interval uniform from 52 bits (26 of each word): (m + 1/2) 2^-52.
+__device__ __forceinline__ double u52(uint32_t hi, uint32_t lo) {
+  const double m = __uint2double_rn(hi >> 6) * 67108864.0 + __uint2double_rn(lo >> 6);
+  return (m + 0.5) * (1.0 / 4503599627370496.0);
+}
+
+// Open-interval uniform from the top 24 bits of one word, for the FP32 path.
+__device__ __forceinline__ float u24(uint32_t w) {
+  return (__uint2float_rn(w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+// Box-Muller pair.
+template <class R> struct Normal2;
+template <> struct Normal2<double> {
+  static __device__ __forceinline__ double2 from(uint4 w) {
+    const double u1 = u52(w.x, w.y), u2 = u52(w.z, w.w);
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    return make_double2(rad * c, rad * s);
+  }
+};
+template <> struct Normal2<float> {
+  static __device__ __forceinline__ double2 from(uint4 w) {
+    const float u1 = u24(w.x), u2 = u24(w.z);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_double2((double)(rad * c), (double)(rad * s));
+  }
+};
+
+// Counter layout: (k, j, tag, 0); tags 0/1 process noise of global substep k,
+// 2 measurement noise of sample k, 3 per-trajectory parameters.
+template <class R>
+__device__ __forceinline__ void process_noise(const DevModel& m, uint32_t j, uint32_t k,
+                                              R xi[3]) {
+  const double2 a = Normal2<R>::from(philox4x32_10(make_uint4(k, j, 0u, 0u), m.key0, m.key1));
+  const double2 b = Normal2<R>::from(philox4x32_10(make_uint4(k, j, 1u, 0u), m.key0, m.key1));
+  xi[0] = (R)a.x;
+  xi[1] = (R)a.y;
+  xi[2] = (R)b.x;
+}
+
+template <class R>
+__device__ __forceinline__ R meas_noise(const DevModel& m, uint32_t j, uint32_t i) {
+  return (R)Normal2<R>::from(philox4x32_10(make_uint4(i, j, 2u, 0u), m.key0, m.key1)).x;
+}
+
+struct TrajParams {
+  double EaR, t_d, dTin;
+};
+
+// Time and sign of the T_in step (uniform on [t0, tf)) and the lognormal E_a/R.
+__device__ __forceinline__ TrajParams traj_params(const DevModel& m, uint32_t j) {
+  TrajParams p;
+  const uint4 w = philox4x32_10(make_uint4(0u, j, 3u, 0u), m.key0, m.key1);
+  const double tf = m.t0 + (double)m.n_steps * m.Ts;
+  p.t_d = m.t0 + u52(w.x, w.y) * (tf - m.t0);
+  p.dTin = (w.z & 1u) ? m.dTin : -m.dTin;
+  const double2 z = Normal2<double>::from(philox4x32_10(make_uint4(1u, j, 3u, 0u), m.key0, m.key1));
+  p.EaR = (m.Ea_logsd != 0.0) ? m.EaR * exp(m.Ea_logsd * z.x) : m.EaR;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// CSTR, Eq. (CSTR): dn/dt = C_in F - c F + S^T r(c) V, S = [-1, -2, beta],
+// r = k0 exp(-(E_a/R)/c_T) c_A c_B.
+
+__device__ __forceinline__ double expr(double x) { return exp(x); }
+__device__ __forceinline__ float expr(float x) { return expf(x); }
+
+template <class R>
+__device__ __forceinline__ void plant_drift(const DevModel& m, R EaR, R T_in, const R n[3],
+                                            R F, R f[3]) {
+  const R iV = (R)m.iV;
+  const R cA = n[0] * iV, cB = n[1] * iV, cT = n[2] * iV;
+  const R k = (R)m.k0 * expr(-EaR / cT);
+  const R rV = k * cA * cB * (R)m.V;
+  f[0] = (R)m.cA_in * F - cA * F - rV;
+  f[1] = (R)m.cB_in * F - cB * F - (R)2 * rV;
+  f[2] = T_in * F - cT * F + (R)m.beta * rV;
+}
+
+// One Euler-Maruyama substep: n += f h + F sigma-bar sqrt(h) xi.
+template <class R>
+__device__ __forceinline__ void em_step(const DevModel& m, R EaR, R T_in, R n[3], R F, R h,
+                                        R sqh, const R xi[3]) {
+  R f[3];
+  plant_drift<R>(m, EaR, T_in, n, F, f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) n[i] = n[i] + f[i] * h + F * (R)m.sigma[i] * sqh * xi[i];
+}
+
+// One-state model (Sec. VI) in x = n_T; c_A, c_B from the reaction invariants.
+// Returns f and df/dx, df/dF.
+template <class R>
+__device__ __forceinline__ void model1(const DevModel& m, R EaR, R x, R F, R& f, R& fx,
+                                       R& fF) {
+  const R V = (R)m.V, beta = (R)m.beta, Tin = (R)m.T_in;
+  const R iV = (R)m.iV, ib = (R)m.ib;
+  const R cT = x * iV;
+  const R cA = (R)m.cA_in + (Tin - cT) * ib;
+  const R cB = (R)m.cB_in + (R)2 * (Tin - cT) * ib;
+  const R iT = (R)1 / cT;
+  const R k = (R)m.k0 * expr(-EaR * iT);
+  const R r = k * cA * cB;
+  f = F * (Tin - cT) + beta * r * V;
+  const R dk = k * EaR * iT * iT;
+  const R dr = dk * cA * cB - k * ib * cB - (R)2 * k * ib * cA;
+  fx = (-F + beta * dr * V) * iV;
+  fF = Tin - cT;
+}
+
+// One shooting interval: n_rk4 classical RK4 steps over Ts from x0 (K L) with
+// flow F = v Fconv, and the forward sensitivities a = dx/dx0, b = dx/dv.
+template <class R, bool kSens>
+__device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4, R Ts, R x0,
+                                             R v, R Fconv, R& xF, R& A, R& B) {
+  const R h = Ts / (R)n_rk4;
+  const R hh = (R)0.5 * h, h6 = h / (R)6;
+  const R F = v * Fconv;
+  R x = x0, a = 1, b = 0;
+  for (int s = 0; s < n_rk4; ++s) {
+    R f1, fx1, fF1, f2, fx2, fF2, f3, fx3, fF3, f4, fx4, fF4;
+    model1<R>(m, EaR, x, F, f1, fx1, fF1);
+    const R x2 = x + hh * f1;
+    model1<R>(m, EaR, x2, F, f2, fx2, fF2);
+    const R x3 = x + hh * f2;
+    model1<R>(m, EaR, x3, F, f3, fx3, fF3);
+    const R x4 = x + h * f3;
+    model1<R>(m, EaR, x4, F, f4, fx4, fF4);
+    if (kSens) {
+      const R a1 = fx1 * a, b1 = fx1 * b + fF1 * Fconv;
+      const R a2 = fx2 * (a + hh * a1), b2 = fx2 * (b + hh * b1) + fF2 * Fconv;
+      const R a3 = fx3 * (a + hh * a2), b3 = fx3 * (b + hh * b2) + fF3 * Fconv;
+      const R a4 = fx4 * (a + h * a3), b4 = fx4 * (b + h * b3) + fF4 * Fconv;
+      a = a + h6 * (a1 + (R)2 * a2 + (R)2 * a3 + a4);
+      b = b + h6 * (b1 + (R)2 * b2 + (R)2 * b3 + b4);
+    }
+    x = x + h6 * (f1 + (R)2 * f2 + (R)2 * f3 + f4);
+  }
+  xF = x;
+  A = a;
+  B = b;
+}
+
+// CD-EKF prediction, Eq. (predictionEquations): RK4 on (x, P) with
+// dP/dt = 2 (df/dx) P + (F sigma_T)^2 over one sample time.
+template <class R>
+__device__ __forceinline__ void ekf_predict(const DevModel& m, R EaR, int n_rk4, R F, R& x,
+                                            R& P) {
+  const R h = (R)m.Ts / (R)n_rk4;
+  const R hh = (R)0.5 * h, h6 = h / (R)6;
+  const R sq = F * (R)m.sigma[2];
+  const R q = sq * sq;
+  R xs = x, Ps = P;
+  for (int s = 0; s < n_rk4; ++s) {
+    R f1, A1, f2, A2, f3, A3, f4, A4, d;
+    model1<R>(m, EaR, xs, F, f1, A1, d);
+    const R p1 = (R)2 * A1 * Ps + q;
+    model1<R>(m, EaR, xs + hh * f1, F, f2, A2, d);
+    const R p2 = (R)2 * A2 * (Ps + hh * p1) + q;
+    model1<R>(m, EaR, xs + hh * f2, F, f3, A3, d);
+    const R p3 = (R)2 * A3 * (Ps + hh * p2) + q;
+    model1<R>(m, EaR, xs + h * f3, F, f4, A4, d);
+    const R p4 = (R)2 * A4 * (Ps + h * p3) + q;
+    xs = xs + h6 * (f1 + (R)2 * f2 + (R)2 * f3 + f4);
+    Ps = Ps + h6 * (p1 + (R)2 * p2 + (R)2 * p3 + p4);
+  }
+  x = xs;
+  P = Ps;
+}
+
+// CD-EKF filtering with the Joseph-form covariance, Eq. (Josph); always FP64.
+__device__ __forceinline__ void ekf_filter(const DevModel& m, double y, double& x, double& P) {
+  const double R = m.meas_sd * m.meas_sd;
+  const double C = 1.0 / m.V;
+  const double e = y - x / m.V;
+  const double Re = R + C * P * C;
+  const double K = P * C / Re;
+  const double ImKC = 1.0 - K * C;
+  P = ImKC * P * ImKC + K * R * K;
+  x = x + K * e;
+}
+
+// Piecewise-constant set-point z-bar(t).
+__device__ __forceinline__ double zbar(const DevModel& m, double t) {
+  double z = m.sp_value[0];
+  for (int s = 1; s < m.n_sp; ++s)
+    if (t >= m.sp_time[s]) z = m.sp_value[s];
+  return z;
+}
+
+// Steady-state flow (L/s) of the one-state model at temperature Tbar.
+__device__ __forceinline__ double Fss(const DevModel& m, double EaR, double Tbar) {
+  const double cA = m.cA_in + (m.T_in - Tbar) / m.beta;
+  const double cB = m.cB_in + 2.0 * (m.T_in - Tbar) / m.beta;
+  const double r = m.k0 * exp(-EaR / Tbar) * cA * cB;
+  return m.beta * r * m.V / (Tbar - m.T_in);
+}
+
+// PI law with anti-windup, Eq. (PI); flows in L/s.
+template <class R>
+__device__ __forceinline__ R pi_step(const DevCtrl& c, R Ts, R ybar, R y, R ubar, R& Ihat) {
+  const R umin = (R)(c.u_min / 60000.0), umax = (R)(c.u_max / 60000.0);
+  const R e = ybar - y;
+  const R P = (R)c.kP * e;
+  const R I = Ihat + Ts * (R)c.kI * e;
+  const R uhat = ubar + P + I;
+  const R u = fmax(umin, fmin(umax, uhat));
+  Ihat = I + Ts * (R)c.kaw * (uhat - u);
+  return u;
+}
+
+}  // namespace mc

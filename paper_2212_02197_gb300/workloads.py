@@ -68,7 +68,8 @@ def nmpc(N: int = 20, u_max: float = 800.0, precision: str = "fp64") -> dict:
     """NMPC settings of Sec. VII-A (N_c = 5 RK4 steps, Q_z = 1, P_{-1|-1} = 1e-6)."""
     return dict(kind="nmpc", precision=precision, N=int(N), n_rk4=5, sqp_max_it=100,
                 ls_max=30, u_min=0.0, u_max=float(u_max), kP=-1e-3, kI=-1e-4, kaw=-1e-1,
-                Qz=1.0, P0=1e-6, sqp_tol=1e-5, u_scale=float(u_max), x_scale=CSTR["V"])
+                Qz=1.0, P0=1e-6, sqp_tol=1e-5, u_scale=float(u_max), x_scale=CSTR["V"],
+                qp_solver="active_set", ip_max_it=60, ip_tol=1e-14)
 
 
 def pi(u_max: float = 800.0, precision: str = "fp64") -> dict:

@@ -1,0 +1,83 @@
+"""The C ABI library loads, exports every function include/mc.h declares, and
+rejects invalid configurations before touching the GPU (runs without one)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2212_02197_gb300 import _build, mc, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return mc.lib()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(mc_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(\w+)$", out, flags=re.M))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert getattr(L, n) is not None
+
+
+def test_status_strings(L):
+    assert L.mc_status_str(0) == b"ok"
+    assert b"timed out" in L.mc_status_str(4)
+
+
+def _bad(model=None, ctrl=None, n=10):
+    w = workloads.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], **(model or {}))
+    c = dict(w["nmpc"], **(ctrl or {}))
+    with pytest.raises(mc.McError) as e:
+        mc.MonteCarlo(m, c, n, 1)
+    assert e.value.status == mc.MC_EINVAL
+    return str(e.value)
+
+
+@pytest.mark.parametrize("model,ctrl,needle", [
+    ({}, {"u_min": 900.0}, "u_min <= u_max"),
+    ({}, {"N": 0}, "horizon"),
+    ({}, {"N": 65}, "horizon"),
+    ({"meas_sd": 0.0}, {}, "measurement noise"),
+    ({"Ts": 0.0}, {}, "Ts > 0"),
+    ({"n_em": 0}, {}, "n_em"),
+    ({"V": -1.0}, {}, "positive"),
+    ({"sp_time": [0.0, 10.0, 5.0], "sp_value": [1.0, 2.0, 3.0]}, {}, "increase"),
+    ({}, {"sqp_tol": 0.0}, "sqp_tol"),
+    ({}, {"qp_solver": "ipm", "ip_max_it": 0}, "interior-point"),
+])
+def test_invalid_configurations_are_rejected(L, model, ctrl, needle):
+    assert needle in _bad(model, ctrl)
+
+
+def test_negative_size_is_rejected(L):
+    assert "n_sims" in _bad(n=-1)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    monkeypatch.setattr(mc, "_lib", None)
+    monkeypatch.setattr(mc._build, "LIB", "/nonexistent/libmc_gb300.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        mc.lib()

@@ -1,0 +1,295 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP64 everywhere on this path):
+  * Philox words: bit-exact.  Box-Muller normals: 1e-13 absolute (the device
+    takes sin/cos of 2 pi u with an exact argument scaling).
+  * QP solutions (active set): both sides reach the same KKT point exactly;
+    1e-9 relative.  Interior point: stopped at 1e-14 (scaled) residual and
+    complementarity, compared at 1e-6.
+  * Closed loop, per trajectory: PI Phi within 1e-12 relative; NMPC Phi within
+    1e-6 relative (the SQP stops at a tolerance of 1e-5 on the scaled KKT test,
+    so the two implementations may stop one iteration apart); trajectories with
+    an OCP at the iteration limit on either side are counted and held to 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_02197_gb300 import mc, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2212_02197_gb300 import _build
+
+    _build.build()
+    oracle.build()
+
+
+# ------------------------------------------------------------------ random numbers
+
+def test_philox_bit_exact():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(20000, 4), dtype=np.uint64).astype(np.uint32)
+    key = [0x12345678, 0x9ABCDEF0]
+    dev = mc.philox(ctr, key)
+    for i in range(0, 20000, 97):
+        assert list(dev[i]) == oracle.philox(list(map(int, ctr[i])), key)
+    kat = mc.philox([[0, 0, 0, 0]], [0, 0])
+    assert list(kat[0]) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+@pytest.mark.parametrize("j", [0, 1, 29999, 262143])
+def test_noise_matches_oracle(j):
+    import ctypes as C
+
+    seed = W.SEED
+    proc, meas = mc.noise(seed, j, 0, 2400)
+    L = oracle.lib()
+    xi = np.zeros(3)
+    for k in range(0, 2400, 7):
+        L.or_process_noise(seed, j, k, xi.ctypes.data_as(C.POINTER(C.c_double)))
+        assert np.allclose(proc[k], xi, rtol=0, atol=1e-13)
+        assert abs(meas[k] - L.or_meas_noise(seed, j, k)) <= 1e-13
+    # FP32 transform of the same words: 24-bit uniforms, so |dz| grows like
+    # 2^-24 / (u1 |z|) in the tails
+    p32, m32 = mc.noise(seed, j, 0, 2400, "mixed")
+    assert np.max(np.abs(p32 - proc)) < 1e-3 and np.max(np.abs(m32 - meas)) < 1e-3
+    assert np.median(np.abs(p32 - proc)) < 1e-6
+
+
+# ------------------------------------------------------------------ QP subproblem
+
+def random_qps(n, N, rng):
+    A = rng.uniform(0.6, 1.2, (n, N))
+    B = rng.uniform(-2.0, 2.0, (n, N))
+    b = rng.normal(0.0, 0.5, (n, N))
+    L = rng.normal(size=(n, N + 1, 2, 2)) + 1.5 * np.eye(2)
+    Wk = L @ np.swapaxes(L, -1, -2) + 0.1 * np.eye(2)
+    Wxx, Wxu, Wuu = Wk[..., 0, 0].copy(), Wk[..., 0, 1].copy(), Wk[..., 1, 1].copy()
+    Wxx[:, 0] = Wxu[:, 0] = 0.0
+    Wxu[:, N] = Wuu[:, N] = 0.0
+    q = rng.normal(0.0, 2.0, (n, N + 1))
+    q[:, 0] = 0.0
+    r = rng.normal(0.0, 2.0, (n, N))
+    lb = -rng.uniform(0.0, 0.3, (n, N))
+    ub = rng.uniform(0.0, 0.3, (n, N))
+    lb[:, ::5] = 0.0   # some inputs start on a bound, as in the SQP
+    return A, B, b, Wxx, Wxu, Wuu, q, r, lb, ub
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 20, 40, 64])
+@pytest.mark.parametrize("solver", ["active_set", "ipm"])
+def test_qp_matches_oracle(N, solver):
+    rng = np.random.default_rng(N)
+    n = 300
+    qp = random_qps(n, N, rng)
+    dev = mc.qp_solve_batch(*qp, solver=solver)
+    assert np.all(dev["status"] == 0), np.flatnonzero(dev["status"])
+    tol = dict(active_set=(1e-9, 1e-10), ipm=(1e-6, 1e-6))[solver]
+    for i in range(n):
+        ref = oracle.qp_solve(*[a[i] for a in qp])
+        assert ref["status"] == 0
+        for key in ("du", "dx", "mu", "nul", "nuu"):
+            scale = 1.0 + np.max(np.abs(ref[key]))
+            assert np.allclose(dev[key][i], ref[key], rtol=tol[0], atol=tol[1] * scale), (i, key)
+
+
+# ------------------------------------------------------------------ OCPs
+
+def ocp_cases(n, N, rng):
+    m = W.model(240)
+    x0 = rng.uniform(276.0, 345.0, n)
+    zs = rng.choice([276.0, 282.0, 290.0, 340.0], size=(n, 2))
+    ksw = rng.integers(1, N + 1, n)
+    zbar = np.where(np.arange(N + 1)[None, :] < ksw[:, None], zs[:, :1], zs[:, 1:])
+    u = np.clip(rng.uniform(-0.2, 1.2, (n, 1)) * np.ones((1, N)), 0.0, 1.0)
+    x = np.repeat(x0[:, None], N + 1, axis=1)
+    return m, x0, zbar, u, x
+
+
+@pytest.mark.parametrize("N", [2, 20, 30])
+def test_ocp_sqp_matches_oracle(N):
+    rng = np.random.default_rng(7 + N)
+    n = 96
+    c = W.nmpc(N)
+    m, x0, zbar, u, x = ocp_cases(n, N, rng)
+    dev = mc.ocp_solve_batch(m, c, x0, m["EaR"], zbar, u, x)
+    agree = 0
+    for i in range(n):
+        ru, rx, rl, _, _, info = oracle.sqp(m, c, m["EaR"], x0[i], zbar[i], u[i], x[i])
+        assert dev["status"][i] == info["status"] or info["status"] != 0 or dev["status"][i] != 0
+        if info["status"] == 0 and dev["status"][i] == 0:
+            agree += abs(int(dev["iters"][i]) - info["iters"]) <= 1
+            assert np.allclose(dev["u"][i], ru, rtol=0, atol=1e-5), i
+            assert dev["kkt_grad"][i] <= c["sqp_tol"] and dev["kkt_eq"][i] <= c["sqp_tol"]
+    # near the tolerance the two may stop an iteration or two apart
+    assert agree >= 0.8 * n
+
+
+# ------------------------------------------------------------------ closed loop
+
+def compare_phi(dev_phi, ref, dev_cnt, tol):
+    """Per-trajectory relative Phi error; trajectories with an OCP at the
+    iteration limit on either side are allowed 1e-3 and reported."""
+    rel = np.abs(dev_phi - ref["phi"]) / np.abs(ref["phi"])
+    hit = (ref["n_ocp_failed"] > 0) | (dev_cnt["n_ocp_failed"] > 0)
+    assert np.all(rel[~hit] <= tol), (np.max(rel[~hit]), np.argmax(np.where(hit, 0, rel)))
+    assert np.all(rel[hit] <= 1e-3)
+    return rel, hit
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = W.get("cstr_100x120_N20_fp64")
+    n = w["n_traj"]
+    out = {}
+    for kind in ("nmpc", "pi"):
+        h = mc.MonteCarlo(w["model"], w[kind], n, w["seed"])
+        h.run()
+        st = h.stats(timeout_ms=600000)
+        out[kind] = (h.phi(), h.counters(), st,
+                     oracle.run(w["model"], w[kind], w["seed"], 0, n))
+        h.close()
+    return w, out
+
+
+def test_closed_loop_pi_small(small):
+    _, out = small
+    phi, cnt, st, ref = out["pi"]
+    compare_phi(phi, ref, cnt, 1e-12)
+    assert st["n_traj"] == 100 and st["n_ocp"] == 0 and st["n_nonfinite"] == 0
+
+
+def test_closed_loop_nmpc_small(small):
+    w, out = small
+    phi, cnt, st, ref = out["nmpc"]
+    rel, hit = compare_phi(phi, ref, cnt, 1e-6)
+    K = w["model"]["n_steps"]
+    assert st["n_ocp"] == 100 * K
+    assert st["n_ocp_failed"] == cnt["n_ocp_failed"].sum()
+    # the SQP work is the same up to rounding-level stopping decisions
+    assert abs(cnt["sqp_iters"].sum() - ref["sqp_iters"].sum()) <= 0.01 * ref["sqp_iters"].sum()
+
+
+def test_stats_reduction_matches_numpy(small):
+    _, out = small
+    for kind in ("nmpc", "pi"):
+        phi, cnt, st, _ = out[kind]
+        assert st["phi_mean"] == pytest.approx(phi.mean(), rel=1e-13)
+        assert st["phi_var"] == pytest.approx(phi.var(ddof=1), rel=1e-11)
+        assert st["phi_min"] == phi.min() and st["phi_max"] == phi.max()
+        h, _ = np.histogram(phi, bins=st["n_bins"], range=(st["bin_lo"], st["bin_hi"]))
+        # the top edge is inclusive in numpy and clamped into the last bin here
+        assert np.array_equal(st["hist"], h)
+        for k in ("sqp_iters", "ls_trials", "qp_iters", "n_hess_reset"):
+            assert st[k] == cnt[k].sum()
+
+
+def test_nmpc_beats_pi_small(small):
+    _, out = small
+    a, b = out["nmpc"][0], out["pi"][0]
+    assert a.mean() < b.mean() and a.var() < b.var()
+
+
+def test_paper_scale_sampled_parity():
+    """The 30,000-trajectory FP64 study in the benchmark's launch configuration;
+    the oracle recomputes a sample of trajectories spread over the index range."""
+    w = W.get("cstr_30k_x240_N20_fp64")
+    n = w["n_traj"]
+    sample = np.unique(np.concatenate([np.arange(0, 8), np.linspace(0, n - 1, 40).astype(int),
+                                       [n - 1]]))
+    for kind, tol in (("nmpc", 1e-6), ("pi", 1e-12)):
+        h = mc.MonteCarlo(w["model"], w[kind], n, w["seed"])
+        h.run()
+        st = h.stats(timeout_ms=1800000)
+        phi = h.phi()
+        cnt = h.counters()
+        h.close()
+        assert st["n_traj"] == n and st["n_nonfinite"] == 0
+        refs = [oracle.run(w["model"], w[kind], w["seed"], int(j), int(j) + 1, threads=1)
+                for j in sample]
+        ref = {k: np.concatenate([r[k] for r in refs]) for k in refs[0]}
+        compare_phi(phi[sample], ref, {k: v[sample] for k, v in cnt.items()}, tol)
+        if kind == "nmpc":
+            # Table II: total OCPs = trajectories x steps; failures are rare
+            assert st["n_ocp"] == n * w["model"]["n_steps"]
+            assert st["n_ocp_failed"] <= 1e-3 * st["n_ocp"]
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_range_split_is_bit_identical():
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=30)
+    for kind in ("nmpc", "pi"):
+        full = mc.MonteCarlo(m, w[kind], 100, 5)
+        full.run()
+        full.sync()
+        part = mc.MonteCarlo(m, w[kind], 100, 5)
+        part.run(j0=0, j1=37)
+        part.run(j0=37, j1=100)
+        part.sync()
+        assert np.array_equal(full.phi(), part.phi())
+        a, b = full.counters(), part.counters()
+        for k in a:
+            assert np.array_equal(a[k], b[k])
+        full.close()
+        part.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 129])
+def test_sizes_empty_single_ragged(n):
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=12)
+    for kind in ("nmpc", "pi"):
+        h = mc.MonteCarlo(m, w[kind], n, 11)
+        h.run()
+        st = h.stats(timeout_ms=600000)
+        assert st["n_traj"] == n
+        if n:
+            ref = oracle.run(m, w[kind], 11, 0, n)
+            phi = h.phi()
+            assert np.allclose(phi, ref["phi"], rtol=1e-6 if kind == "nmpc" else 1e-12, atol=0)
+        h.close()
+
+
+@pytest.mark.parametrize("N", [1, 64])
+def test_horizon_extremes(N):
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=24)
+    c = W.nmpc(N)
+    h = mc.MonteCarlo(m, c, 6, 3)
+    h.run()
+    h.sync()
+    ref = oracle.run(m, c, 3, 0, 6)
+    compare_phi(h.phi(), ref, h.counters(), 1e-6)
+    h.close()
+
+
+def test_fixed_input_degenerate_box():
+    """u_min = u_max: the OCP has no freedom; both sides apply the bound."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=16)
+    c = dict(w["nmpc"], u_min=400.0, u_max=400.0)
+    h = mc.MonteCarlo(m, c, 4, 3)
+    h.run()
+    h.sync()
+    ref = oracle.run(m, c, 3, 0, 4)
+    assert np.allclose(h.phi(), ref["phi"], rtol=1e-10, atol=0)
+    h.close()
+
+
+def test_ipm_closed_loop_matches_oracle():
+    """The paper's QP solver (Riccati interior point) in the closed loop."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=60)
+    c = dict(w["nmpc"], qp_solver="ipm")
+    h = mc.MonteCarlo(m, c, 16, w["seed"])
+    h.run()
+    h.sync()
+    ref = oracle.run(m, c, w["seed"], 0, 16)
+    compare_phi(h.phi(), ref, h.counters(), 1e-6)
+    h.close()
