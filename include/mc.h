@@ -214,6 +214,39 @@ mc_status mc_ocp_solve_batch(const mc_model_t* model, const mc_controller_t* ctr
                              const double* zbar, double* u, double* x, double* lam,
                              double* pil, double* piu, int32_t* info, double* kkt);
 
+/* ---------------------------------------------------------------------------
+ * Statistics without allocation.  The paper has no counterpart to this call;
+ * it exists for callers that cannot call cudaMalloc: code that runs under a
+ * device-memory budget fixed up front, or in a loop that must never enter the
+ * allocator (cudaMalloc may synchronise the device and its latency is
+ * unbounded), or a host framework that owns all device memory itself.
+ * ------------------------------------------------------------------------- */
+
+/* Largest n one mc_reduce_noalloc call accepts: 1024 blocks of 256 threads. */
+#define MC_NOALLOC_MAX_TRAJ 262144
+
+/* Reduce per-trajectory results that already live on the device -- phi_dev
+ * (n doubles) and counters_dev (n x MC_N_COUNTERS int32, the layout of
+ * mc_copy_counters; must not be NULL) -- into *out_host, exactly as mc_stats
+ * reduces a run: mean/variance/min/max of the finite Phi, the histogram
+ * (n_bins bins on [lo, hi), lo >= hi meaning [min, max]) and the counter sums.
+ * n_ocp and gpu_ms are left 0 (this call does not know the run).
+ *
+ * Nothing is allocated.  The scratch (1024 block partials and one result
+ * record, about 120 KB) is a file-scope __device__ array in the library: every
+ * GPU that loads the library holds it until the process exits.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array and each call overwrites what it reads, so calls that overlap
+ * on the GPU (other streams, other host threads) race: serialise them.
+ * The call enqueues two kernels on cuda_stream, waits for that stream and
+ * copies the result to out_host.  Returns MC_EINVAL for n < 0,
+ * n > MC_NOALLOC_MAX_TRAJ, n_bins outside 1..MC_MAX_BINS or NULL pointers;
+ * MC_WARN_NONFINITE if some Phi is not finite. */
+mc_status mc_reduce_noalloc(const double* phi_dev, const int32_t* counters_dev, int64_t n,
+                            int32_t n_bins, double lo, double hi, void* cuda_stream,
+                            mc_stats_t* out_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@
 //   k_philox, k_noise, k_qp_batch, k_ocp_batch   building blocks on their own
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -794,6 +795,97 @@ mc_status mc_ocp_solve_batch(const mc_model_t* model, const mc_controller_t* ctr
   }
   for (void* p : owned) cudaFree(p);
   return s;
+}
+
+// ------------------------------------------------------- no-allocation reduce
+
+}  // extern "C"
+
+// Scratch of mc_reduce_noalloc: block partials for at most
+// MC_NOALLOC_MAX_TRAJ / kStatThreads blocks and one result record.  Device
+// code could name these directly; host code must go through the device
+// address that cudaGetSymbolAddress returns (the host-side name is only a
+// stand-in, not a device address).
+static __device__ __align__(256) Partial g_noalloc_part[MC_NOALLOC_MAX_TRAJ / kStatThreads];
+static __device__ __align__(256) DevStats g_noalloc_stats;
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+Partial* g_noalloc_part_ptr[kMaxDevices] = {};
+DevStats* g_noalloc_stats_ptr[kMaxDevices] = {};
+
+// Device addresses of the scratch on the current device; looked up once per
+// device, with that device current.
+cudaError_t noalloc_scratch(Partial** part, DevStats** st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_part_ptr[dev]) {
+    void* p = nullptr;
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_part);
+    if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress(&q, g_noalloc_stats);
+    if (e != cudaSuccess) return e;
+    g_noalloc_part_ptr[dev] = (Partial*)p;
+    g_noalloc_stats_ptr[dev] = (DevStats*)q;
+  }
+  *part = g_noalloc_part_ptr[dev];
+  *st = g_noalloc_stats_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+mc_status mc_reduce_noalloc(const double* phi_dev, const int32_t* counters_dev, int64_t n,
+                            int32_t n_bins, double lo, double hi, void* cuda_stream,
+                            mc_stats_t* out_host) {
+  if (!phi_dev || !counters_dev || !out_host)
+    return fail(nullptr, MC_EINVAL, "mc_reduce_noalloc: null pointer");
+  if (n < 0 || n > MC_NOALLOC_MAX_TRAJ)
+    return fail(nullptr, MC_EINVAL,
+                "mc_reduce_noalloc: n must be in 0..262144 (MC_NOALLOC_MAX_TRAJ), the size "
+                "of its static scratch");
+  if (n_bins < 1 || n_bins > MC_MAX_BINS)
+    return fail(nullptr, MC_EINVAL, "mc_reduce_noalloc: n_bins must be 1..256");
+  Partial* part = nullptr;
+  DevStats* dst = nullptr;
+  cudaError_t e = noalloc_scratch(&part, &dst);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "mc_reduce_noalloc: scratch address");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int nb = (int)((n + kStatThreads - 1) / kStatThreads);
+  if (nb < 1) nb = 1;
+  k_stats_partial<<<nb, kStatThreads, 0, st>>>(phi_dev, counters_dev, 0, n, part);
+  k_stats_final<<<1, kStatThreads, 0, st>>>(part, nb, phi_dev, 0, n, n_bins, lo, hi, dst);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "mc_reduce_noalloc: launch");
+  DevStats d;
+  e = cudaMemcpyAsync(&d, dst, sizeof(d), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "mc_reduce_noalloc: result copy");
+  memset(out_host, 0, sizeof(*out_host));
+  out_host->n_traj = n;
+  out_host->n_ocp_failed = d.sums[0];
+  out_host->sqp_iters = d.sums[1];
+  out_host->ls_trials = d.sums[2];
+  out_host->n_hess_reset = d.sums[3];
+  out_host->n_ls_fail = d.sums[4];
+  out_host->qp_iters = d.sums[5];
+  out_host->n_nonfinite = d.n_nonfinite;
+  out_host->qp_fail = d.sums[7];
+  out_host->phi_mean = d.mean;
+  out_host->phi_var = (d.n > 1) ? d.m2 / (d.n - 1.0) : 0.0;
+  out_host->phi_min = d.mn;
+  out_host->phi_max = d.mx;
+  out_host->n_bins = n_bins;
+  out_host->bin_lo = d.lo;
+  out_host->bin_hi = d.hi;
+  for (int b = 0; b < MC_MAX_BINS; ++b) out_host->hist[b] = d.hist[b];
+  return d.n_nonfinite > 0 ? MC_WARN_NONFINITE : MC_OK;
 }
 
 }  // extern "C"

@@ -106,9 +106,12 @@ def lib():
                                              C.c_double] + [_dp] * 15 + [_ip, _ip])
             L.mc_ocp_solve_batch.argtypes = ([C.POINTER(McModel), C.POINTER(McController),
                                               C.c_int64] + [_dp] * 8 + [_ip, _dp])
+            L.mc_reduce_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                            C.c_double, C.c_double, C.c_void_p,
+                                            C.POINTER(McStats)]
             for f in ("mc_create", "mc_set_histogram", "mc_run", "mc_run_range", "mc_stats",
                       "mc_copy_phi", "mc_copy_counters", "mc_sync", "mc_philox", "mc_noise",
-                      "mc_qp_solve_batch", "mc_ocp_solve_batch"):
+                      "mc_qp_solve_batch", "mc_ocp_solve_batch", "mc_reduce_noalloc"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -225,6 +228,13 @@ class MonteCarlo:
         _check(lib().mc_copy_phi(self._h, j0, n, a.ctypes.data_as(C.c_void_p), 0), self._h)
         return a
 
+    def counters_to(self, out, j0: int = 0, n: int | None = None):
+        """Per-trajectory counters copied device to device into `out` (a CUDA
+        torch tensor of n x N_COUNTERS int32)."""
+        n = self.n_sims - j0 if n is None else n
+        _check(lib().mc_copy_counters(self._h, j0, n, C.c_void_p(out.data_ptr()), 1), self._h)
+        return out
+
     def counters(self, j0: int = 0, n: int | None = None) -> dict:
         n = self.n_sims - j0 if n is None else n
         a = np.empty((n, N_COUNTERS), dtype=np.int32)
@@ -293,3 +303,26 @@ def ocp_solve_batch(model: dict, ctrl: dict, x0, EaR, zbar, u, x, lam=None, pil=
     return dict(u=u, x=x, lam=lam, pil=pil, piu=piu, iters=info[:, 0], status=info[:, 1],
                 ls_trials=info[:, 2], qp_iters=info[:, 3], kkt_grad=kkt[:, 0], kkt_eq=kkt[:, 1],
                 f=kkt[:, 2])
+
+
+MAX_NOALLOC_TRAJ = 262144
+
+
+def _stats_dict(s: McStats, st: int) -> dict:
+    d = {f: getattr(s, f) for f, _ in McStats._fields_ if f not in ("hist", "reserved0")}
+    d["hist"] = np.array(s.hist[: s.n_bins], dtype=np.int64)
+    d["status"] = st
+    return d
+
+
+def reduce_noalloc(phi_dev, counters_dev, n: int, n_bins: int = 64, lo: float = 0.0,
+                   hi: float = 0.0, stream=None) -> dict:
+    """Statistics of per-trajectory results already on the device (CUDA torch
+    tensors: n float64 and n x N_COUNTERS int32), reduced without any device
+    allocation (see mc_reduce_noalloc in include/mc.h)."""
+    s = McStats()
+    ptr = lambda t: C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    st = _check(lib().mc_reduce_noalloc(ptr(phi_dev), ptr(counters_dev), n, n_bins, lo, hi,
+                                        _stream_ptr(stream), C.byref(s)),
+                ok=(MC_OK, MC_WARN_NONFINITE))
+    return _stats_dict(s, st)
