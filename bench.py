@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2212_02197_gb300 import workloads as W  # noqa: E402
+from paper_2212_02197_gb300 import shards, workloads as W  # noqa: E402
 
 METRIC = "closed-loop trajectories/sec (NMPC CSTR, 30k sims) mixed vs FP64, at stated tol"
 DEFAULT_WORKLOAD = "cstr_30k_x240_N20_fp64"
@@ -262,6 +262,8 @@ def main():
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     nmpc_ms = [a.elapsed_time(b) for a, b, c in ev]
     st_n = h_n.stats()
+    # the study's statistics over all ranks (only the reduced numbers travel)
+    st_all = shards.allgather_stats(st_n, dist if world > 1 else None)
     my_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([my_ms], device=dev)
@@ -308,6 +310,8 @@ def main():
     h2d = 2 * (8 * len(w["model"]["sp_time"]) * 2 + 400)
     d2h = 8 * T * (2 if w["pi"] is not None else 1) + 2 * 2400
 
+    st_pall = shards.allgather_stats(h_p.stats(), dist if world > 1 else None) \
+        if h_p is not None else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -321,18 +325,18 @@ def main():
                            "l2": "512 MB buffer written between timed steps",
                            "parallelism": f"trajectory shards x{world}"},
                 "nmpc_ms_per_step": statistics.mean(nmpc_ms),
-                "ocp_stats": {k: st_n[k] for k in ("n_ocp", "n_ocp_failed", "n_ls_fail",
-                                                   "sqp_iters", "ls_trials", "qp_iters",
-                                                   "n_hess_reset")},
-                "phi": {"nmpc_mean": st_n["phi_mean"], "nmpc_var": st_n["phi_var"]},
+                "ocp_stats": {k: st_all[k] for k in ("n_ocp", "n_ocp_failed", "n_ls_fail",
+                                                     "sqp_iters", "ls_trials", "qp_iters",
+                                                     "n_hess_reset")},
+                "phi": {"nmpc_mean": st_all["phi_mean"], "nmpc_var": st_all["phi_var"],
+                        "n_traj": st_all["n_traj"]},
                 "gpu_launches": args.steps * (3 + (3 if h_p is not None else 0)),
                 "roofline": roofline,
                 "clocks": clk, "wall_s_timed": wall,
                 "e2e": {"value": world * T / (e2e_ms_step / 1e3), "unit": "trajectories/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
         if h_p is not None:
-            st_p = h_p.stats()
-            line["phi"].update(pi_mean=st_p["phi_mean"], pi_var=st_p["phi_var"])
+            line["phi"].update(pi_mean=st_pall["phi_mean"], pi_var=st_pall["phi_var"])
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

@@ -24,7 +24,8 @@ namespace mc {
 
 // --------------------------------------------------------------- kernels
 
-__global__ void __launch_bounds__(128) k_nmpc(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
+template <class R>
+__global__ void __launch_bounds__(32) k_nmpc(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
                                               double* __restrict__ phi,
                                               int32_t* __restrict__ cnt, double* ws,
                                               int64_t ld) {
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(128) k_nmpc(DevModel m, DevCtrl c, int64_t j0,
   if (t >= ld) return;
   const Ws w{ws + t, ld, c.N + 1};
   for (int64_t j = j0 + t; j < j1; j += ld) {
-    const TrajOut o = traj_nmpc(m, c, (uint32_t)j, w);
+    const TrajOut o = traj_nmpc<R>(m, c, (uint32_t)j, w);
     phi[j] = o.phi;
 #pragma unroll
     for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
@@ -281,7 +282,8 @@ __global__ void k_ocp_batch(DevModel m, DevCtrl c, int64_t n, OcpBatch d, double
     w(X, k) = d.x[o2 + k];
     w(ZB, k) = d.zbar[o2 + k];
   }
-  const SqpInfo si = sqp_solve(m, c, d.EaR[t], d.x0[t], w);
+  const SqpInfo si = (c.precision == MC_MIXED) ? sqp_solve<float>(m, c, d.EaR[t], d.x0[t], w)
+                                               : sqp_solve<double>(m, c, d.EaR[t], d.x0[t], w);
   for (int k = 0; k < N; ++k) {
     d.u[o1 + k] = w(U, k);
     d.lam[o1 + k] = w(LAM, k);
@@ -310,7 +312,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kNmpcThreads = 128;
+// One warp per block: the FP64 pipe's time on an SM is proportional to the
+// number of warps it holds, so warp-sized blocks spread the trajectories over
+// the 152 SMs as evenly as the warp granularity allows.
+constexpr int kNmpcThreads = 32;
 constexpr int kMaxStatBlocks = 1024;
 
 struct DevBuf {
@@ -387,7 +392,6 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
       return bad("unknown QP solver");
     if (cc->qp_solver == MC_QP_IPM && (cc->ip_max_it < 1 || !(cc->ip_tol > 0)))
       return bad("the interior-point solver needs ip_max_it >= 1 and ip_tol > 0");
-    if (cc->precision == MC_MIXED) return bad("mixed precision is available for PI only");
   }
   memset(m, 0, sizeof(*m));
   m->V = mm->V; m->k0 = mm->k0; m->EaR = mm->EaR; m->beta = mm->beta;
@@ -433,12 +437,14 @@ static int64_t nmpc_threads_for(int64_t n) {
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nmpc, kNmpcThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nmpc<double>, kNmpcThreads, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 4;
   const int64_t cap = (int64_t)sms * per_sm * kNmpcThreads;
-  int64_t t = n < cap ? n : cap;
+  // equal numbers of trajectories per thread when they exceed the resident threads
+  const int64_t passes = (n + cap - 1) / cap;
+  int64_t t = passes > 0 ? (n + passes - 1) / passes : 0;
   t = (t + kNmpcThreads - 1) / kNmpcThreads * kNmpcThreads;
   return t < kNmpcThreads ? kNmpcThreads : t;
 }
@@ -544,8 +550,12 @@ mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) 
       int64_t threads = n < h->ws_ld ? n : h->ws_ld;
       const int64_t blocks = (threads + kNmpcThreads - 1) / kNmpcThreads;
       // the scratch stride is the allocation's, the thread count the range's
-      k_nmpc<<<(unsigned)blocks, kNmpcThreads, 0, st>>>(h->m, h->c, j0, j1, h->phi, h->cnt,
-                                                        h->ws, h->ws_ld);
+      if (h->c.precision == MC_FP64)
+        k_nmpc<double><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(h->m, h->c, j0, j1, h->phi,
+                                                                  h->cnt, h->ws, h->ws_ld);
+      else
+        k_nmpc<float><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(h->m, h->c, j0, j1, h->phi,
+                                                                 h->cnt, h->ws, h->ws_ld);
     } else {
       const int64_t blocks = (j1 - j0 + 127) / 128;
       if (h->c.precision == MC_FP64)

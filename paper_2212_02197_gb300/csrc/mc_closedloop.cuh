@@ -64,6 +64,11 @@ __device__ TrajOut traj_pi(const DevModel& m, const DevCtrl& c, uint32_t j) {
   return out;
 }
 
+// R = double: the FP64 path.  R = float: the mixed-precision path -- plant
+// SDE, noise transform, EKF prediction and the OCP shooting in FP32; the
+// Joseph-form filter update, the QP (Riccati pivots), merit, BFGS and the SQP
+// convergence test in FP64.
+template <class R>
 __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, const Ws& w) {
   TrajOut out{};
   const TrajParams tp = traj_params(m, j);
@@ -98,11 +103,16 @@ __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, co
     phi += ez * ez;
     if (i == K) break;
 
-    const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
-    if (i > 0) ekf_predict<double>(m, EaR, c.n_rk4, F_prev, xhat, P);
+    const double y = cT + m.meas_sd * (double)meas_noise<R>(m, j, (uint32_t)i);
+    if (i > 0) {
+      R xr = (R)xhat, Pr = (R)P;
+      ekf_predict<R>(m, (R)EaR, c.n_rk4, (R)F_prev, xr, Pr);
+      xhat = (double)xr;
+      P = (double)Pr;
+    }
     ekf_filter(m, y, xhat, P);
     for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(i + k) * m.Ts);
-    const SqpInfo si = sqp_solve(m, c, EaR, xhat * ixs, w);
+    const SqpInfo si = sqp_solve<R>(m, c, EaR, xhat * ixs, w, i > 0);
     out.cnt[0] += (si.status == 1);
     out.cnt[1] += si.iters;
     out.cnt[2] += si.ls_trials;
@@ -111,15 +121,19 @@ __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, co
     out.cnt[5] += si.qp_iters;
     out.cnt[7] += si.qp_fail;
     const double F = w(U, 0) * c.Fconv;
-    // receding horizon: shift one interval, duplicating the last one
+    // receding horizon: shift one interval, duplicating the last one; the
+    // final evaluation shifts along (its intervals 1..N-2 stay valid)
     for (int k = 0; k < N - 1; ++k) {
       w(U, k) = w(U, k + 1);
       w(X, k + 1) = w(X, k + 2);
       w(LAM, k) = w(LAM, k + 1);
       w(PIL, k) = w(PIL, k + 1);
       w(PIU, k) = w(PIU, k + 1);
+      w(EA, k) = w(EA, k + 1);
+      w(EB, k) = w(EB, k + 1);
+      w(EG, k) = w(EG, k + 1);
     }
-    plant_interval<double>(m, tp, j, i, F, n);
+    plant_interval<R>(m, tp, j, i, F, n);
     F_prev = F;
   }
   out.phi = phi / (double)(K + 1);

@@ -18,22 +18,32 @@ struct SqpInfo {
 
 // Shooting of all N intervals at the point (u_arr, x_arr) with sensitivities,
 // writing A_k, B_k, g_k and q_k into (a_arr, b_arr, g_arr, q_arr); returns the
-// objective f = sum_k Q_z (z_k - zbar_k)^2 T_s.
+// objective f = sum_k Q_z (z_k - zbar_k)^2 T_s.  With reuse_mid the intervals
+// 1 .. N-2 keep the A_k, B_k, g_k already in the arrays: after the receding-
+// horizon shift they are the previous OCP's values at the same (x_k, u_k), so
+// only the first and the last interval are integrated again.
+// R is the arithmetic of the RK4 integration (FP32 on the mixed-precision
+// path); the constraint residual g_k, the objective and its gradient are FP64.
+template <class R>
 __device__ __forceinline__ double evaluate(const DevModel& m, const DevCtrl& c, double EaR,
                                            double x0, const Ws& w, int u_arr, int x_arr,
-                                           int a_arr, int b_arr, int g_arr, int q_arr) {
+                                           int a_arr, int b_arr, int g_arr, int q_arr,
+                                           bool reuse_mid = false) {
   const int N = c.N;
   const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
   const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
   double f = 0.0;
   double xk = x0;
   for (int k = 0; k < N; ++k) {
-    double Fn, a, b;
-    rk4_interval<double, true>(m, EaR, c.n_rk4, m.Ts, xk * xs, w(u_arr, k), c.Fconv, Fn, a, b);
     const double xn = w(x_arr, k + 1);
-    w(a_arr, k) = a;
-    w(b_arr, k) = b * ixs;
-    w(g_arr, k) = Fn * ixs - xn;
+    if (!(reuse_mid && k >= 1 && k <= N - 2)) {
+      R Fn, a, b;
+      rk4_interval<R, true>(m, (R)EaR, c.n_rk4, (R)m.Ts, (R)(xk * xs), (R)w(u_arr, k),
+                            (R)c.Fconv, Fn, a, b);
+      w(a_arr, k) = (double)a;
+      w(b_arr, k) = (double)b * ixs;
+      w(g_arr, k) = (double)Fn * ixs - xn;
+    }
     const double dz = xn * xs * m.iV - w(ZB, k + 1);
     f += c.Qz * dz * dz * m.Ts;
     w(q_arr, k + 1) = qf * dz;
@@ -74,8 +84,12 @@ __device__ __forceinline__ void bfgs_block(int n, double& w11, double& w12, doub
 // SQP of Sec. IV for one OCP from the warm start in (U, X, LAM, PIL, PIU); the
 // set-points z-bar(t_{i+k}) are in ZB[1..N].  Returns diagnostics; the
 // solution (or the last iterate on failure) is left in U, X and the multipliers.
+// With shifted_eval the evaluation arrays hold the previous OCP's final
+// evaluation shifted by one interval (see evaluate).  R is the shooting
+// arithmetic; everything else (QP, merit, BFGS, convergence test) is FP64.
+template <class R>
 __device__ __noinline__ SqpInfo sqp_solve(const DevModel& m, const DevCtrl& c, double EaR,
-                                          double x0, const Ws& w) {
+                                          double x0, const Ws& w, bool shifted_eval = false) {
   const int N = c.N;
   const double c1 = 1e-4, s_max = 100.0;
   SqpInfo info{};
@@ -85,7 +99,7 @@ __device__ __noinline__ SqpInfo sqp_solve(const DevModel& m, const DevCtrl& c, d
     w(WUU, k) = 1.0;
   }
   w(X, 0) = x0;
-  double f = evaluate(m, c, EaR, x0, w, U, X, EA, EB, EG, EQ);
+  double f = evaluate<R>(m, c, EaR, x0, w, U, X, EA, EB, EG, EQ, shifted_eval);
   double alpha = 0.0;
   int nqp = 0;
   for (int l = 0;; ++l) {
@@ -195,7 +209,7 @@ __device__ __noinline__ SqpInfo sqp_solve(const DevModel& m, const DevCtrl& c, d
         w(UT, k) = fmin(fmax(w(U, k) + alpha * w(DU, k), c.vmin), c.vmax);
         w(XT, k + 1) = w(X, k + 1) + alpha * w(DX, k + 1);
       }
-      ft = evaluate(m, c, EaR, x0, w, UT, XT, TA, TB, TG, TQ);
+      ft = evaluate<R>(m, c, EaR, x0, w, UT, XT, TA, TB, TG, TQ);
       info.ls_trials++;
       double pt = 0.0;
       for (int k = 0; k < N; ++k) pt += w(SIG, k) * fabs(w(TG, k));
