@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     # smaller cases of the same workload, for profiling captures
     ap.add_argument("--n-traj", type=int, default=None)
     ap.add_argument("--n-steps", type=int, default=None)
@@ -282,6 +283,58 @@ def main():
                 "kernel": "k_nmpc (FP64, one thread per trajectory)",
                 "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak available)"}
 
+    # the same study in mixed precision, timed the same way and accepted
+    # against this FP64 run (mean of Phi within 0.5 %, KS statistic < 0.01)
+    mixed = None
+    wl32 = args.workload.replace("_fp64", "_mixed")
+    if not args.no_mixed and wl32 in W.WORKLOADS and wl32 != args.workload:
+        w32 = W.get(wl32)
+        w32["model"] = w["model"]
+        h32 = mc.MonteCarlo(w32["model"], w32["nmpc"], j1, w32["seed"])
+        h32p = mc.MonteCarlo(w32["model"], w32["pi"], j1, w32["seed"])
+        for _ in range(max(1, args.warmup)):
+            h32.run(stream, j0, j1)
+            h32p.run(stream, j0, j1)
+        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                 torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier()
+        for a, b, c in ev32:
+            flush.zero_()
+            a.record(stream)
+            h32.run(stream, j0, j1)
+            b.record(stream)
+            h32p.run(stream, j0, j1)
+            c.record(stream)
+        barrier()
+        m_ms = statistics.mean(a.elapsed_time(c) for a, b, c in ev32)
+        m_nmpc_ms = statistics.mean(a.elapsed_time(b) for a, b, c in ev32)
+        st32 = h32.stats()
+        phi64, phi32 = h_n.phi(j0, T), h32.phi(j0, T)
+        try:
+            from scipy import stats as sps
+            ks = float(sps.ks_2samp(phi32, phi64).statistic)
+        except Exception:
+            ks = None
+        mean_rel = st32["phi_mean"] / st_n["phi_mean"] - 1.0
+        if world > 1:
+            t = torch.tensor([m_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            m_ms = float(t.item())
+        f32 = nmpc_flops(w32["model"], w32["nmpc"], T, st32)
+        mixed = {"workload": wl32, "value": world * T / (m_ms / 1e3), "unit": "trajectories/s",
+                 "ms_per_step": m_ms, "nmpc_ms_per_step": m_nmpc_ms,
+                 "speedup_vs_fp64": ms_per_step / m_ms,
+                 "dtype": "f32 shooting/plant/EKF-predict + f64 Joseph/QP/merit/BFGS/KKT",
+                 "sqp_tol": w32["nmpc"]["sqp_tol"], "ls_max": w32["nmpc"]["ls_max"],
+                 "phi_mean_rel_vs_fp64": mean_rel, "ks_vs_fp64": ks,
+                 "median_rel_err_vs_fp64": float(np.median(np.abs(phi32 - phi64) / np.abs(phi64))),
+                 "accepted": bool(abs(mean_rel) < 5e-3 and ks is not None and ks < 1e-2),
+                 "ocp_stats": {k: st32[k] for k in ("n_ocp", "n_ocp_failed", "n_ls_fail",
+                                                    "sqp_iters", "ls_trials")},
+                 "algorithmic_tflops": f32 / (m_nmpc_ms / 1e3) / 1e12}
+        h32.close()
+        h32p.close()
+
     # end to end through the C ABI with host buffers: create (config h2d),
     # run, stats and Phi copied back to host, destroy
     e2e_ms = []
@@ -337,6 +390,8 @@ def main():
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
         if h_p is not None:
             line["phi"].update(pi_mean=st_pall["phi_mean"], pi_var=st_pall["phi_var"])
+        if mixed is not None:
+            line["mixed"] = mixed
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
