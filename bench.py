@@ -33,30 +33,46 @@ from paper_2212_02197_gb300 import shards, workloads as W  # noqa: E402
 
 METRIC = "closed-loop trajectories/sec (NMPC CSTR, 30k sims) mixed vs FP64, at stated tol"
 DEFAULT_WORKLOAD = "cstr_30k_x240_N20_fp64"
-# nominal FP64 rate of a GB300 (no measured FP64 peak in MEASURED_PEAKS.json)
-FP64_PEAK_TFLOPS = 1.25
 
 
 # ------------------------------------------------------------------ algorithmic work
+#
+# The NMPC kernel is bound by GB300's FP64 pipe (2 DFMA per SM per clock).  Its
+# algorithmic work is counted in FP64 pipe operations: each add, multiply or
+# fused multiply-add of the method is one operation, and each elementary
+# function costs what it costs on that pipe, measured on a GB300 in DFMA
+# equivalents by a throughput micro-benchmark (see the design notes).
+W_EXP, W_DIV, W_LOG, W_SQRT, W_SINCOS = 16.9, 5.6, 29.3, 8.6, 26.7
+# per unit, from the kernel source (one state, one input):
+OPS_MODEL1 = 24 + W_EXP + W_DIV               # f, df/dx, df/dF of the one-state model
+OPS_RK4_SENS = 4 * OPS_MODEL1 + 33            # one RK4 step with forward sensitivities
+OPS_INTERVAL_EXTRA = 8                        # g_k, q_k, objective term
+OPS_QP_STAGE = 24 + W_DIV                     # active-set iteration, per stage
+OPS_SQP_STAGE = 45 + 2 * W_DIV                # gradient, KKT test, block BFGS, merit
+OPS_ACCEPT_STAGE = 15 + W_DIV                 # multiplier step, gradients, copy
+OPS_TRIAL_STAGE = 6                           # trial point and its merit sum
+OPS_EKF = 5 * (4 * (20 + W_EXP + W_DIV) + 12) + 12 + W_DIV   # predict (N_c = 5) + filter
+OPS_EM = 38 + W_EXP + W_DIV - 5.6 + 12 + 2 * (8 + W_LOG + W_SQRT + W_SINCOS)  # substep
+PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
 
-def nmpc_flops(cfg_model, cfg_ctrl, n_traj, st):
-    """Algorithmic FP64 operations of one NMPC launch (fma = 2, each divide,
-    square root or transcendental = 1), from the counters the kernel reports:
-      RK4 step of the one-state model with sensitivities: 200
-      SQP evaluation (shooting of N intervals):           N * n_rk4 * 200
-      active-set QP iteration (Riccati sweeps, tests):    40 per stage
-      SQP iteration bookkeeping (gradient, KKT, BFGS, merit): 60 per stage
-      CD-EKF prediction (n_rk4 RK4 steps of x and P) + filter: 170 n_rk4 + 15
-      Euler-Maruyama substep incl. two Box-Muller pairs:   60
-    """
+
+def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st):
+    """FP64 pipe operations of one NMPC launch from the counters it reports."""
     N, nrk = cfg_ctrl["N"], cfg_ctrl["n_rk4"]
     K, nem = cfg_model["n_steps"], cfg_model["n_em"]
-    evals = st["n_ocp"] + st["ls_trials"]
-    f = evals * N * nrk * 200.0
-    f += st["qp_iters"] * N * 40.0
-    f += st["sqp_iters"] * N * 60.0
-    f += n_traj * K * (170.0 * nrk + 15.0 + nem * 60.0 + 40.0)
-    return f
+    per_interval = nrk * OPS_RK4_SENS + OPS_INTERVAL_EXTRA
+    first_evals = n_traj * N + (st["n_ocp"] - n_traj) * min(N, 2)   # warm starts reuse N-2
+    ops = (first_evals + st["ls_trials"] * N) * per_interval
+    ops += st["qp_iters"] * N * OPS_QP_STAGE
+    ops += st["sqp_iters"] * N * (OPS_SQP_STAGE + OPS_ACCEPT_STAGE)
+    ops += st["ls_trials"] * N * OPS_TRIAL_STAGE
+    ops += n_traj * K * (OPS_EKF + nem * OPS_EM)
+    return ops
+
+
+def nmpc_flops(cfg_model, cfg_ctrl, n_traj, st):
+    """DFMA-equivalent flops (2 per FP64 pipe operation)."""
+    return 2.0 * nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st)
 
 
 # ------------------------------------------------------------------ clocks
@@ -189,6 +205,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     # smaller cases of the same workload, for profiling captures
     ap.add_argument("--n-traj", type=int, default=None)
     ap.add_argument("--n-steps", type=int, default=None)
@@ -225,6 +242,9 @@ def main():
     j0, j1 = rank * T, (rank + 1) * T
     h_n = mc.MonteCarlo(w["model"], w["nmpc"], j1, w["seed"])
     h_p = mc.MonteCarlo(w["model"], w["pi"], j1, w["seed"]) if w["pi"] is not None else None
+    tuned_tps = None
+    if w["nmpc"].get("schedule") == "persistent" and not args.no_autotune:
+        tuned_tps = h_n.autotune(probe_steps=24, stream=stream)   # set-up, untimed
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
@@ -278,10 +298,13 @@ def main():
     flops = nmpc_flops(w["model"], w["nmpc"], T, st_n)
     k_ms = statistics.mean(nmpc_ms)
     achieved = flops / (k_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_nmpc (FP64, one thread per trajectory)",
-                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak available)"}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_nmpc_persist<double> (FP64 pipe)",
+                "work": "FP64 pipe operations x 2 (DFMA-equivalent flops), elementary "
+                        "functions weighted by their measured DFMA cost",
+                "peak_source": "2 DFMA/clk/SM x 152 SMs x 2.07 GHz (no FP64 figure in "
+                               "the measured peaks; the FP64 probe sustains 84 % of it)"}
 
     # the same study in mixed precision, timed the same way and accepted
     # against this FP64 run (mean of Phi within 0.5 %, KS statistic < 0.01)
@@ -321,7 +344,8 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             m_ms = float(t.item())
         f32 = nmpc_flops(w32["model"], w32["nmpc"], T, st32)
-        mixed = {"workload": wl32, "value": world * T / (m_ms / 1e3), "unit": "trajectories/s",
+        mixed = {"workload": wl32, "schedule": w32["nmpc"].get("schedule", "static"),
+                 "value": world * T / (m_ms / 1e3), "unit": "trajectories/s",
                  "ms_per_step": m_ms, "nmpc_ms_per_step": m_nmpc_ms,
                  "speedup_vs_fp64": ms_per_step / m_ms,
                  "dtype": "f32 shooting/plant/EKF-predict + f64 Joseph/QP/merit/BFGS/KKT",
@@ -375,6 +399,8 @@ def main():
                            "n_steps": w["model"]["n_steps"], "N": w["nmpc"]["N"],
                            "precision": w["nmpc"]["precision"],
                            "qp_solver": w["nmpc"]["qp_solver"],
+                           "schedule": w["nmpc"].get("schedule", "static"),
+                           "threads_per_sm": tuned_tps,
                            "l2": "512 MB buffer written between timed steps",
                            "parallelism": f"trajectory shards x{world}"},
                 "nmpc_ms_per_step": statistics.mean(nmpc_ms),

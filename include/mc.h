@@ -100,7 +100,22 @@ typedef struct {
   double ip_tol;          /* interior-point residual/complementarity tolerance */
   double u_scale;         /* OCP input unit (mL/min)                           */
   double x_scale;         /* OCP state unit (K L); V makes it kelvin           */
+  /* uneven batches: > 0 draws each trajectory's horizon uniformly from
+   * N_min..N and its SQP iteration limit from sqp_max_it_min..sqp_max_it
+   * (Philox counter (2, j, 3, 0)); 0 keeps N and sqp_max_it for all         */
+  int32_t N_min;
+  int32_t sqp_max_it_min;
+  int32_t schedule;       /* mc_schedule                                       */
+  int32_t threads_per_sm; /* persistent schedule: resident threads per SM,
+                             0 = one per trajectory up to the GPU's capacity   */
 } mc_controller_t;
+
+typedef enum {
+  MC_SCHED_STATIC = 0,    /* one thread per trajectory, OCPs in lock-step      */
+  MC_SCHED_PERSISTENT = 1 /* per-lane state machine, shared line-search
+                             shooting, trajectories taken from a queue (longest
+                             horizons first when horizons differ)             */
+} mc_schedule;
 
 /* Reduced results of the last run (Table II and Fig. 3 of Sec. VII). */
 typedef struct {
@@ -146,6 +161,20 @@ mc_status mc_run(mc_handle* h, void* cuda_stream);
  * the statistics over that range.  Per-trajectory results of other indices
  * are kept. */
 mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream);
+
+/* CUDA graphs: with on = 1 each trajectory range's launch sequence is
+ * captured into a graph on its first mc_run/mc_run_range and replayed from
+ * then on; on = 0 (default) launches directly.  Needs a stream other than the
+ * legacy default stream (with NULL the launches stay direct).  Changing the
+ * histogram or autotuning drops the captured graphs. */
+mc_status mc_set_graph(mc_handle* h, int on);
+
+/* Persistent NMPC schedule only: time short probe runs (the first probe_steps
+ * samples of every trajectory) for a range of resident threads per SM, keep
+ * the fastest in the handle and return it in *threads_per_sm (may be NULL).
+ * Blocks until done; overwrites the per-trajectory results of earlier runs. */
+mc_status mc_autotune(mc_handle* h, int32_t probe_steps, void* cuda_stream,
+                      int32_t* threads_per_sm);
 
 /* Wait for the last run (polling, at most timeout_ms; <= 0 waits without limit)
  * and copy its statistics.  Returns MC_ETIMEOUT if the GPU has not finished,

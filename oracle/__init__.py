@@ -60,7 +60,7 @@ class Ctrl(C.Structure):
                 ("u_min", C.c_double), ("u_max", C.c_double), ("kP", C.c_double),
                 ("kI", C.c_double), ("kaw", C.c_double), ("Qz", C.c_double),
                 ("P0", C.c_double), ("sqp_tol", C.c_double), ("u_scale", C.c_double),
-                ("x_scale", C.c_double)]
+                ("x_scale", C.c_double), ("N_min", C.c_int32), ("it_min", C.c_int32)]
 
 
 class TrajOut(C.Structure):
@@ -117,6 +117,8 @@ def lib():
                                  _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(SqpInfo)]
             L.or_sqp.restype = C.c_int
             L.or_bfgs_block.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.or_traj_horizon.argtypes = [C.POINTER(Ctrl), C.c_uint64, C.c_int64,
+                                          C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.or_pi_step.argtypes = [C.POINTER(Ctrl), C.c_double, C.c_double, C.c_double,
                                      C.c_double, _dp]
             L.or_pi_step.restype = C.c_double
@@ -158,6 +160,8 @@ def make_ctrl(cd: dict) -> Ctrl:
     for k in ("u_min", "u_max", "kP", "kI", "kaw", "Qz", "P0", "sqp_tol", "u_scale",
               "x_scale"):
         setattr(c, k, float(cd[k]))
+    c.N_min = int(cd.get("N_min", 0))
+    c.it_min = int(cd.get("sqp_max_it_min", 0))
     assert 1 <= c.N <= MAX_N
     return c
 
@@ -327,3 +331,11 @@ def traj_params(model: dict, seed, j):
     a, b, c = C.c_double(), C.c_double(), C.c_double()
     L.or_traj_params(C.byref(m), seed, j, C.byref(a), C.byref(b), C.byref(c))
     return a.value, b.value, c.value
+
+
+def traj_horizon(ctrl: dict, seed, j):
+    L = lib()
+    c = make_ctrl(ctrl)
+    N, it = C.c_int(), C.c_int()
+    L.or_traj_horizon(C.byref(c), seed, j, C.byref(N), C.byref(it))
+    return N.value, it.value

@@ -36,10 +36,14 @@ static void trace_row(double* trace, int i, double T, double y, double xhat, dou
   r[0] = T; r[1] = y; r[2] = xhat; r[3] = u; r[4] = it;
 }
 
-void or_traj(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j,
+void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
              or_traj_out* out, double* trace) {
   double EaR, t_d, dTin;
   or_traj_params(m, seed, j, &EaR, &t_d, &dTin);
+  /* this trajectory's horizon and SQP iteration limit (uneven batches) */
+  or_ctrl cj = *c_in;
+  or_traj_horizon(c_in, seed, j, &cj.N, &cj.sqp_max_it);
+  const or_ctrl* c = &cj;
   memset(out, 0, sizeof(*out));
 
   /* plant initialised with the feed, x_0 = n_0 = C_in V (Sec. VII-A) */

@@ -107,3 +107,16 @@ void or_traj_params(const or_model* m, uint64_t seed, int64_t j, double* EaR_j,
   or_normal_pair(w, z);
   *EaR_j = (m->Ea_logsd != 0.0) ? m->EaR * exp(m->Ea_logsd * z[0]) : m->EaR;
 }
+
+/* Uneven batches: the OCP horizon and SQP iteration limit of trajectory j,
+ * uniform integers from the first two words of counter (2, j, 3, 0). */
+void or_traj_horizon(const or_ctrl* c, uint64_t seed, int64_t j, int* N, int* max_it) {
+  uint32_t w[4];
+  *N = c->N;
+  *max_it = c->sqp_max_it;
+  if (c->N_min <= 0 && c->it_min <= 0) return;
+  draw(seed, 2u, (uint32_t)j, 3u, w);
+  if (c->N_min > 0) *N = c->N_min + (int)(w[0] % (uint32_t)(c->N - c->N_min + 1));
+  if (c->it_min > 0)
+    *max_it = c->it_min + (int)(w[1] % (uint32_t)(c->sqp_max_it - c->it_min + 1));
+}

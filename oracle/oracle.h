@@ -70,6 +70,8 @@ typedef struct {
   double sqp_tol;       /* epsilon of the scaled convergence test            */
   double u_scale;       /* unit of the OCP input variable, in mL/min         */
   double x_scale;       /* unit of the OCP state variable, in K L            */
+  int32_t N_min;        /* > 0: per-trajectory horizon uniform on N_min..N   */
+  int32_t it_min;       /* > 0: per-trajectory SQP limit on it_min..max_it   */
 } or_ctrl;
 
 /* Per-trajectory result of one closed-loop simulation. */
@@ -107,6 +109,7 @@ void or_process_noise(uint64_t seed, int64_t j, int64_t substep, double xi[3]);
 double or_meas_noise(uint64_t seed, int64_t j, int64_t step);
 void or_traj_params(const or_model* m, uint64_t seed, int64_t j,
                     double* EaR_j, double* t_d, double* dTin);
+void or_traj_horizon(const or_ctrl* c, uint64_t seed, int64_t j, int* N, int* max_it);
 
 /* ---- CSTR model, Eq. (CSTR) ---- */
 void or_plant_drift(const or_model* m, double EaR, double T_in, const double n[3],

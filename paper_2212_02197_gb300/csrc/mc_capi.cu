@@ -41,6 +41,20 @@ __global__ void __launch_bounds__(32) k_nmpc(DevModel m, DevCtrl c, int64_t j0, 
 }
 
 template <class R>
+__global__ void __launch_bounds__(32) k_nmpc_persist(DevModel m, DevCtrl c, int64_t j0,
+                                                     int64_t n, const uint32_t* order,
+                                                     unsigned long long* next,
+                                                     double* __restrict__ phi,
+                                                     int32_t* __restrict__ cnt, double* ws,
+                                                     int64_t ld) {
+  // launched with whole warps and at most ld threads; every lane takes part in
+  // the warp votes of nmpc_persistent
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Ws w{ws + t, ld, c.N + 1};
+  nmpc_persistent<R>(m, c, w, j0, n, order, next, phi, cnt);
+}
+
+template <class R>
 __global__ void __launch_bounds__(128) k_pi(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
                                             double* __restrict__ phi,
                                             int32_t* __restrict__ cnt) {
@@ -335,6 +349,16 @@ struct mc_handle {
   int32_t* cnt = nullptr;      // n_sims x kNCounters
   double* ws = nullptr;        // NMPC scratch: kNArr * (N+1) x ws_ld
   int64_t ws_ld = 0;
+  int schedule = MC_SCHED_STATIC;
+  uint32_t* order = nullptr;   // trajectories, longest horizon first (uneven batches)
+  unsigned long long* next = nullptr;  // queue position of the persistent schedule
+  int64_t persist_threads = 0;
+  bool use_graph = false;
+  struct Graph {
+    int64_t j0, j1;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;   // captured runs, by trajectory range
   Partial* part = nullptr;     // kMaxStatBlocks
   DevStats* dstats = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -392,6 +416,13 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
       return bad("unknown QP solver");
     if (cc->qp_solver == MC_QP_IPM && (cc->ip_max_it < 1 || !(cc->ip_tol > 0)))
       return bad("the interior-point solver needs ip_max_it >= 1 and ip_tol > 0");
+    if (cc->N_min < 0 || cc->N_min > cc->N) return bad("need 0 <= N_min <= N");
+    if (cc->sqp_max_it_min < 0 || cc->sqp_max_it_min > cc->sqp_max_it)
+      return bad("need 0 <= sqp_max_it_min <= sqp_max_it");
+    if (cc->schedule != MC_SCHED_STATIC && cc->schedule != MC_SCHED_PERSISTENT)
+      return bad("unknown schedule");
+    if (cc->threads_per_sm < 0 || cc->threads_per_sm > 2048)
+      return bad("threads_per_sm must be 0..2048");
   }
   memset(m, 0, sizeof(*m));
   m->V = mm->V; m->k0 = mm->k0; m->EaR = mm->EaR; m->beta = mm->beta;
@@ -415,6 +446,7 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   c->u_min = cc->u_min; c->u_max = cc->u_max; c->kP = cc->kP; c->kI = cc->kI; c->kaw = cc->kaw;
   c->Qz = cc->Qz; c->P0 = cc->P0; c->sqp_tol = cc->sqp_tol; c->ip_tol = cc->ip_tol;
   c->u_scale = cc->u_scale; c->x_scale = cc->x_scale;
+  c->N_min = cc->N_min; c->it_min = cc->sqp_max_it_min;
   if (cc->kind == MC_CTRL_NMPC) {
     c->Fconv = cc->u_scale / 60000.0;
     c->vmin = cc->u_min / cc->u_scale;
@@ -468,13 +500,18 @@ const char* mc_last_error(const mc_handle* h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }
 
+static void drop_graphs(mc_handle* h);
+
 void mc_destroy(mc_handle* h) {
   if (!h) return;
+  drop_graphs(h);
   cudaFree(h->phi);
   cudaFree(h->cnt);
   cudaFree(h->ws);
   cudaFree(h->part);
   cudaFree(h->dstats);
+  cudaFree(h->order);
+  cudaFree(h->next);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -493,6 +530,7 @@ mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl, int64_
     return fail(nullptr, MC_EINVAL, why);
   }
   h->n_sims = n_sims;
+  h->schedule = ctrl->schedule;
   auto alloc = [&](void** p, size_t bytes) -> bool {
     if (bytes == 0) bytes = 8;
     return cudaMalloc(p, bytes) == cudaSuccess;
@@ -504,7 +542,38 @@ mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl, int64_
   if (ok && h->c.kind == MC_CTRL_NMPC && n_sims > 0) {
     h->ws_ld = nmpc_threads_for(n_sims);
     const size_t words = (size_t)kNArr * (h->c.N + 1) * (size_t)h->ws_ld;
-    ok = alloc((void**)&h->ws, words * sizeof(double));
+    ok = alloc((void**)&h->ws, words * sizeof(double)) &&
+         alloc((void**)&h->next, sizeof(unsigned long long));
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t pt = h->ws_ld;
+    if (ctrl->threads_per_sm > 0) {
+      const int64_t want = ((int64_t)ctrl->threads_per_sm * sms + 31) / 32 * 32;
+      pt = want < pt ? want : pt;
+    }
+    h->persist_threads = pt;
+    if (ok && (h->c.N_min > 0 || h->c.it_min > 0)) {
+      // queue order: longest horizon (then highest iteration limit) first, so
+      // the warps take trajectories of equal horizon and the long ones start
+      // early; a counting sort on the host, once per handle
+      std::vector<uint32_t> ord((size_t)n_sims);
+      std::vector<int64_t> bucket((size_t)(MC_MAX_HORIZON + 1) * 128 + 1, 0);
+      std::vector<int> key((size_t)n_sims);
+      for (int64_t j = 0; j < n_sims; ++j) {
+        int Nj, itj;
+        traj_horizon(h->c, h->m.key0, h->m.key1, (uint32_t)j, Nj, itj);
+        const int itk = itj < 127 ? itj : 127;
+        key[(size_t)j] = (MC_MAX_HORIZON - Nj) * 128 + (127 - itk);
+        bucket[(size_t)key[(size_t)j] + 1]++;
+      }
+      for (size_t b = 1; b < bucket.size(); ++b) bucket[b] += bucket[b - 1];
+      for (int64_t j = 0; j < n_sims; ++j)
+        ord[(size_t)bucket[(size_t)key[(size_t)j]]++] = (uint32_t)j;
+      ok = alloc((void**)&h->order, sizeof(uint32_t) * n_sims) &&
+           cudaMemcpy(h->order, ord.data(), sizeof(uint32_t) * n_sims,
+                      cudaMemcpyHostToDevice) == cudaSuccess;
+    }
   }
   if (!ok) {
     cudaGetLastError();
@@ -525,6 +594,7 @@ mc_status mc_set_histogram(mc_handle* h, int32_t n_bins, double lo, double hi) {
   h->n_bins = n_bins;
   h->bin_lo = lo;
   h->bin_hi = hi;
+  drop_graphs(h);  // the bins are baked into captured runs
   return MC_OK;
 }
 
@@ -539,38 +609,147 @@ static mc_status launch_stats(mc_handle* h, int64_t j0, int64_t j1, cudaStream_t
   return MC_OK;
 }
 
-mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) {
-  if (!h) return MC_EINVAL;
-  if (j0 < 0 || j1 < j0 || j1 > h->n_sims) return fail(h, MC_EINVAL, "bad trajectory range");
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  MC_CUDA(h, cudaEventRecord(h->ev0, st));
+}  // extern "C"
+
+// The launches of one run of trajectories j0 .. j1-1 (closed loops and
+// reductions), enqueued on st; the NMPC model may be a shortened copy (probe
+// runs of the autotuner).
+static mc_status enqueue_run(mc_handle* h, const DevModel& m, int64_t j0, int64_t j1,
+                             int64_t persist_threads, cudaStream_t st) {
   if (j1 > j0) {
-    if (h->c.kind == MC_CTRL_NMPC) {
+    if (h->c.kind == MC_CTRL_NMPC && h->schedule == MC_SCHED_PERSISTENT) {
+      const int64_t n = j1 - j0;
+      int64_t threads = n < persist_threads ? n : persist_threads;
+      threads = (threads + kNmpcThreads - 1) / kNmpcThreads * kNmpcThreads;
+      if (threads > h->ws_ld) threads = h->ws_ld;
+      const uint32_t* order = (j0 == 0 && j1 == h->n_sims) ? h->order : nullptr;
+      MC_CUDA(h, cudaMemsetAsync(h->next, 0, sizeof(unsigned long long), st));
+      const unsigned blocks = (unsigned)(threads / kNmpcThreads);
+      if (h->c.precision == MC_FP64)
+        k_nmpc_persist<double><<<blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, n, order, h->next,
+                                                               h->phi, h->cnt, h->ws, h->ws_ld);
+      else
+        k_nmpc_persist<float><<<blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, n, order, h->next,
+                                                              h->phi, h->cnt, h->ws, h->ws_ld);
+    } else if (h->c.kind == MC_CTRL_NMPC) {
       const int64_t n = j1 - j0;
       int64_t threads = n < h->ws_ld ? n : h->ws_ld;
       const int64_t blocks = (threads + kNmpcThreads - 1) / kNmpcThreads;
       // the scratch stride is the allocation's, the thread count the range's
       if (h->c.precision == MC_FP64)
-        k_nmpc<double><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(h->m, h->c, j0, j1, h->phi,
+        k_nmpc<double><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, j1, h->phi,
                                                                   h->cnt, h->ws, h->ws_ld);
       else
-        k_nmpc<float><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(h->m, h->c, j0, j1, h->phi,
+        k_nmpc<float><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, j1, h->phi,
                                                                  h->cnt, h->ws, h->ws_ld);
     } else {
       const int64_t blocks = (j1 - j0 + 127) / 128;
       if (h->c.precision == MC_FP64)
-        k_pi<double><<<(unsigned)blocks, 128, 0, st>>>(h->m, h->c, j0, j1, h->phi, h->cnt);
+        k_pi<double><<<(unsigned)blocks, 128, 0, st>>>(m, h->c, j0, j1, h->phi, h->cnt);
       else
-        k_pi<float><<<(unsigned)blocks, 128, 0, st>>>(h->m, h->c, j0, j1, h->phi, h->cnt);
+        k_pi<float><<<(unsigned)blocks, 128, 0, st>>>(m, h->c, j0, j1, h->phi, h->cnt);
     }
     MC_CUDA(h, cudaGetLastError());
   }
-  mc_status s = launch_stats(h, j0, j1, st);
-  if (s != MC_OK) return s;
+  return launch_stats(h, j0, j1, st);
+}
+
+static void drop_graphs(mc_handle* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
+extern "C" {
+
+mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) {
+  if (!h) return MC_EINVAL;
+  if (j0 < 0 || j1 < j0 || j1 > h->n_sims) return fail(h, MC_EINVAL, "bad trajectory range");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  MC_CUDA(h, cudaEventRecord(h->ev0, st));
+  if (h->use_graph && st != nullptr) {
+    // replay the captured launches of this range, capturing them on first use
+    cudaGraphExec_t exec = nullptr;
+    for (const auto& g : h->graphs)
+      if (g.j0 == j0 && g.j1 == j1) exec = g.exec;
+    if (!exec) {
+      MC_CUDA(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const mc_status s = enqueue_run(h, h->m, j0, j1, h->persist_threads, st);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(st, &graph);
+      if (s != MC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaGraphInstantiate");
+      h->graphs.push_back({j0, j1, exec});
+    }
+    MC_CUDA(h, cudaGraphLaunch(exec, st));
+  } else {
+    const mc_status s = enqueue_run(h, h->m, j0, j1, h->persist_threads, st);
+    if (s != MC_OK) return s;
+  }
   MC_CUDA(h, cudaEventRecord(h->ev1, st));
   h->ran = true;
   h->last_j0 = j0;
   h->last_j1 = j1;
+  return MC_OK;
+}
+
+mc_status mc_set_graph(mc_handle* h, int on) {
+  if (!h) return MC_EINVAL;
+  h->use_graph = on != 0;
+  if (!h->use_graph) drop_graphs(h);
+  return MC_OK;
+}
+
+mc_status mc_autotune(mc_handle* h, int32_t probe_steps, void* cuda_stream,
+                      int32_t* threads_per_sm) {
+  if (!h) return MC_EINVAL;
+  if (h->c.kind != MC_CTRL_NMPC || h->schedule != MC_SCHED_PERSISTENT)
+    return fail(h, MC_EINVAL, "mc_autotune tunes the persistent NMPC schedule only");
+  if (probe_steps < 1) return fail(h, MC_EINVAL, "probe_steps must be >= 1");
+  if (h->n_sims == 0) return MC_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 152;
+  MC_CUDA(h, cudaGetDevice(&dev));
+  MC_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevModel probe = h->m;
+  probe.n_steps = probe_steps < h->m.n_steps ? probe_steps : h->m.n_steps;
+  static const int cand[] = {32, 64, 96, 128, 160, 192, 256, 384, 512};
+  float best_ms = 0.f;
+  int best = 0;
+  int64_t best_threads = h->persist_threads;
+  cudaEvent_t a, b;
+  MC_CUDA(h, cudaEventCreate(&a));
+  MC_CUDA(h, cudaEventCreate(&b));
+  for (int ci = 0; ci <= (int)(sizeof(cand) / sizeof(cand[0])); ++ci) {
+    // the candidates, then one thread per trajectory up to the capacity
+    const bool last = ci == (int)(sizeof(cand) / sizeof(cand[0]));
+    const int tps = last ? (int)((h->ws_ld + sms - 1) / sms) : cand[ci];
+    const int64_t threads = (int64_t)tps * sms;
+    if (!last && threads >= h->ws_ld) continue;
+    const int64_t pt = threads < h->ws_ld ? threads : h->ws_ld;
+    MC_CUDA(h, cudaEventRecord(a, st));
+    mc_status s = enqueue_run(h, probe, 0, h->n_sims, pt, st);
+    if (s != MC_OK) return s;
+    MC_CUDA(h, cudaEventRecord(b, st));
+    MC_CUDA(h, cudaEventSynchronize(b));
+    float ms = 0.f;
+    MC_CUDA(h, cudaEventElapsedTime(&ms, a, b));
+    if (best == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = tps;
+      best_threads = pt;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->persist_threads = best_threads;
+  drop_graphs(h);
+  if (threads_per_sm) *threads_per_sm = best;
   return MC_OK;
 }
 

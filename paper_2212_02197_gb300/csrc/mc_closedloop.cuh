@@ -1,6 +1,16 @@
 // mc_closedloop.cuh -- one stochastic closed-loop simulation per thread
 // (Sec. VII): plant SDE by Euler-Maruyama, noisy measurement, controller
 // (NMPC = CD-EKF + SQP, or PI), and the performance index Phi, Eq. (Phi).
+//
+// Two schedules of the NMPC closed loop:
+//   traj_nmpc        one trajectory per thread, SQPs run to completion one after
+//                    the other; the lanes of a warp wait for the slowest OCP
+//   nmpc_persistent  a per-lane state machine: every lane advances its own
+//                    trajectory through the cheap phases until it needs a
+//                    line-search evaluation, and the warp then shoots all
+//                    pending trial points together; finished lanes take the
+//                    next trajectory from a queue.  Same arithmetic per
+//                    trajectory, bit for bit.
 #pragma once
 
 #include "mc_sqp.cuh"
@@ -38,7 +48,7 @@ __device__ __forceinline__ void plant_interval(const DevModel& m, const TrajPara
 template <class R>
 __device__ TrajOut traj_pi(const DevModel& m, const DevCtrl& c, uint32_t j) {
   TrajOut out{};
-  const TrajParams tp = traj_params(m, j);
+  const TrajParams tp = traj_params(m, c, j);
   double n[3] = {m.cA_in * m.V, m.cB_in * m.V, m.T_in * m.V};
   const int K = m.n_steps;
   double phi = 0.0;
@@ -64,80 +74,214 @@ __device__ TrajOut traj_pi(const DevModel& m, const DevCtrl& c, uint32_t j) {
   return out;
 }
 
+// ---------------------------------------------------------------------------
+// NMPC closed loop, split into the steps both schedules share.
+
+struct NmpcTraj {
+  uint32_t j;
+  int i;                   // current sample
+  TrajParams tp;
+  double n[3], xhat, P, F_prev, phi;
+  TrajOut out;
+};
+
+// Trajectory start (Sec. VII-A): plant filled with feed, EKF at x-hat_{-1|-1},
+// first OCP guess u = F_ss(z-bar(t_0)) clipped, states at the estimate.
+__device__ __forceinline__ void nmpc_begin(const DevModel& m, const DevCtrl& c, uint32_t j,
+                                           const Ws& w, NmpcTraj& T) {
+  T.j = j;
+  T.i = 0;
+  T.tp = traj_params(m, c, j);
+  T.n[0] = m.cA_in * m.V;
+  T.n[1] = m.cB_in * m.V;
+  T.n[2] = m.T_in * m.V;
+  T.xhat = m.T_in * m.V;
+  T.P = c.P0;
+  T.F_prev = 0.0;
+  T.phi = 0.0;
+  T.out = TrajOut{};
+  double v0 = Fss(m, T.tp.EaR, zbar(m, m.t0)) / c.Fconv;
+  v0 = fmin(fmax(v0, c.vmin), c.vmax);
+  const double ixs = 1.0 / c.x_scale;
+  for (int k = 0; k < T.tp.N; ++k) {
+    w(U, k) = v0;
+    w(X, k + 1) = T.xhat * ixs;
+    w(LAM, k) = 0.0;
+    w(PIL, k) = 0.0;
+    w(PIU, k) = 0.0;
+  }
+}
+
+// Sample i: Phi term, and unless the trajectory ends there the measurement,
+// the CD-EKF and the start of the OCP.  Returns false when the trajectory is
+// finished (T.out is final).
+template <class R>
+__device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtrl& c,
+                                                 const Ws& w, NmpcTraj& T, SqpState& s) {
+  const int K = m.n_steps, N = T.tp.N;
+  const double t_i = m.t0 + (double)T.i * m.Ts;
+  const double cT = T.n[2] / m.V;
+  if (!isfinite(cT) || !isfinite(T.xhat) || !isfinite(T.P)) {
+    T.out.cnt[6] = 1;
+    T.out.phi = nan("");
+    return false;
+  }
+  const double ez = cT - zbar(m, t_i);
+  T.phi += ez * ez;
+  if (T.i == K) {
+    T.out.phi = T.phi / (double)(K + 1);
+    return false;
+  }
+  const double y = cT + m.meas_sd * (double)meas_noise<R>(m, T.j, (uint32_t)T.i);
+  if (T.i > 0) {
+    R xr = (R)T.xhat, Pr = (R)T.P;
+    ekf_predict<R>(m, (R)T.tp.EaR, c.n_rk4, (R)T.F_prev, xr, Pr);
+    T.xhat = (double)xr;
+    T.P = (double)Pr;
+  }
+  ekf_filter(m, y, T.xhat, T.P);
+  for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(T.i + k) * m.Ts);
+  sqp_start<R>(m, c, T.tp.EaR, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s);
+  return true;
+}
+
+// After the OCP of sample i: count it, apply u_0, shift the warm start (and
+// the final evaluation) one interval, simulate the plant to t_{i+1}.
+template <class R>
+__device__ __forceinline__ void nmpc_apply_body(const DevModel& m, const DevCtrl& c,
+                                                const Ws& w, NmpcTraj& T, const SqpInfo& si) {
+  const int N = T.tp.N;
+  T.out.cnt[0] += (si.status == 1);
+  T.out.cnt[1] += si.iters;
+  T.out.cnt[2] += si.ls_trials;
+  T.out.cnt[3] += si.n_hess_reset;
+  T.out.cnt[4] += (si.status == 2);
+  T.out.cnt[5] += si.qp_iters;
+  T.out.cnt[7] += si.qp_fail;
+  const double F = w(U, 0) * c.Fconv;
+  for (int k = 0; k < N - 1; ++k) {
+    w(U, k) = w(U, k + 1);
+    w(X, k + 1) = w(X, k + 2);
+    w(LAM, k) = w(LAM, k + 1);
+    w(PIL, k) = w(PIL, k + 1);
+    w(PIU, k) = w(PIU, k + 1);
+    w(EA, k) = w(EA, k + 1);
+    w(EB, k) = w(EB, k + 1);
+    w(EG, k) = w(EG, k + 1);
+  }
+  plant_interval<R>(m, T.tp, T.j, T.i, F, T.n);
+  T.F_prev = F;
+  T.i++;
+}
+
+// Code placement as for sqp_check: separate functions on the mixed path.
+template <class R>
+__device__ __noinline__ bool nmpc_sample_call(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                              NmpcTraj& T, SqpState& s) {
+  return nmpc_sample_body<R>(m, c, w, T, s);
+}
+template <class R>
+__device__ __noinline__ void nmpc_apply_call(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                             NmpcTraj& T, const SqpInfo& si) {
+  nmpc_apply_body<R>(m, c, w, T, si);
+}
+template <class R>
+__device__ __forceinline__ bool nmpc_sample(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                            NmpcTraj& T, SqpState& s) {
+  if constexpr (sizeof(R) == 4) return nmpc_sample_call<R>(m, c, w, T, s);
+  else return nmpc_sample_body<R>(m, c, w, T, s);
+}
+template <class R>
+__device__ __forceinline__ void nmpc_apply(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                           NmpcTraj& T, const SqpInfo& si) {
+  if constexpr (sizeof(R) == 4) nmpc_apply_call<R>(m, c, w, T, si);
+  else nmpc_apply_body<R>(m, c, w, T, si);
+}
+
 // R = double: the FP64 path.  R = float: the mixed-precision path -- plant
 // SDE, noise transform, EKF prediction and the OCP shooting in FP32; the
 // Joseph-form filter update, the QP (Riccati pivots), merit, BFGS and the SQP
 // convergence test in FP64.
 template <class R>
 __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, const Ws& w) {
-  TrajOut out{};
-  const TrajParams tp = traj_params(m, j);
-  const double EaR = tp.EaR;
-  double n[3] = {m.cA_in * m.V, m.cB_in * m.V, m.T_in * m.V};
-  const int K = m.n_steps, N = c.N;
-  const double ixs = 1.0 / c.x_scale;
-  double phi = 0.0;
-  double xhat = m.T_in * m.V, P = c.P0;
-  double F_prev = 0.0;
-  {
-    // first OCP guess: steady-state input of the first set-point, clipped
-    double v0 = Fss(m, EaR, zbar(m, m.t0)) / c.Fconv;
-    v0 = fmin(fmax(v0, c.vmin), c.vmax);
-    for (int k = 0; k < N; ++k) {
-      w(U, k) = v0;
-      w(X, k + 1) = xhat * ixs;
-      w(LAM, k) = 0.0;
-      w(PIL, k) = 0.0;
-      w(PIU, k) = 0.0;
+  NmpcTraj T;
+  SqpState s;
+  nmpc_begin(m, c, j, w, T);
+  while (nmpc_sample<R>(m, c, w, T, s)) {
+    while (!sqp_check<R>(c, w, s)) {
+      int r;
+      do {
+        sqp_eval_trial<R>(m, c, T.tp.EaR, w, s);
+        r = sqp_trial_result<R>(c, w, s);
+      } while (r == 2);
+      if (r == 1) break;
     }
+    nmpc_apply<R>(m, c, w, T, s.info);
   }
-  for (int i = 0; i <= K; ++i) {
-    const double t_i = m.t0 + (double)i * m.Ts;
-    const double cT = n[2] / m.V;
-    if (!isfinite(cT) || !isfinite(xhat) || !isfinite(P)) {
-      out.cnt[6] = 1;
-      phi = nan("");
-      break;
-    }
-    const double ez = cT - zbar(m, t_i);
-    phi += ez * ez;
-    if (i == K) break;
+  return T.out;
+}
 
-    const double y = cT + m.meas_sd * (double)meas_noise<R>(m, j, (uint32_t)i);
-    if (i > 0) {
-      R xr = (R)xhat, Pr = (R)P;
-      ekf_predict<R>(m, (R)EaR, c.n_rk4, (R)F_prev, xr, Pr);
-      xhat = (double)xr;
-      P = (double)Pr;
+// Persistent schedule.  Every lane of the warp must call this (it uses warp
+// votes); trajectories come from the queue `next` (positions 0 .. n-1, mapped
+// through `order` when given, else to j0 + position) and are written to
+// phi_out / cnt_out.
+enum LanePhase : int { kNewTraj = 0, kSample = 1, kCheck = 2, kTrial = 3, kDone = 4 };
+
+template <class R>
+__device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w, int64_t j0,
+                                int64_t n, const uint32_t* __restrict__ order,
+                                unsigned long long* next, double* __restrict__ phi_out,
+                                int32_t* __restrict__ cnt_out) {
+  NmpcTraj T;
+  SqpState s;
+  int phase = kNewTraj;
+  for (;;) {
+    // cheap, divergent phases until this lane needs a trial evaluation
+    while (phase != kTrial && phase != kDone) {
+      if (phase == kNewTraj) {
+        const unsigned long long q = atomicAdd(next, 1ull);
+        if (q >= (unsigned long long)n) {
+          phase = kDone;
+          break;
+        }
+        const uint32_t j = order ? order[q] : (uint32_t)(j0 + (int64_t)q);
+        nmpc_begin(m, c, j, w, T);
+        phase = kSample;
+      }
+      if (phase == kSample) {
+        if (nmpc_sample<R>(m, c, w, T, s)) {
+          phase = kCheck;
+        } else {
+          phi_out[T.j] = T.out.phi;
+#pragma unroll
+          for (int q = 0; q < kNCounters; ++q)
+            cnt_out[(int64_t)T.j * kNCounters + q] = T.out.cnt[q];
+          phase = kNewTraj;
+          continue;
+        }
+      }
+      if (phase == kCheck) {
+        if (sqp_check<R>(c, w, s)) {
+          nmpc_apply<R>(m, c, w, T, s.info);
+          phase = kSample;
+        } else {
+          phase = kTrial;
+        }
+      }
     }
-    ekf_filter(m, y, xhat, P);
-    for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(i + k) * m.Ts);
-    const SqpInfo si = sqp_solve<R>(m, c, EaR, xhat * ixs, w, i > 0);
-    out.cnt[0] += (si.status == 1);
-    out.cnt[1] += si.iters;
-    out.cnt[2] += si.ls_trials;
-    out.cnt[3] += si.n_hess_reset;
-    out.cnt[4] += (si.status == 2);
-    out.cnt[5] += si.qp_iters;
-    out.cnt[7] += si.qp_fail;
-    const double F = w(U, 0) * c.Fconv;
-    // receding horizon: shift one interval, duplicating the last one; the
-    // final evaluation shifts along (its intervals 1..N-2 stay valid)
-    for (int k = 0; k < N - 1; ++k) {
-      w(U, k) = w(U, k + 1);
-      w(X, k + 1) = w(X, k + 2);
-      w(LAM, k) = w(LAM, k + 1);
-      w(PIL, k) = w(PIL, k + 1);
-      w(PIU, k) = w(PIU, k + 1);
-      w(EA, k) = w(EA, k + 1);
-      w(EB, k) = w(EB, k + 1);
-      w(EG, k) = w(EG, k + 1);
+    // the shared, expensive part: all lanes with a pending trial shoot it
+    if (!__any_sync(0xffffffffu, phase == kTrial)) break;
+    if (phase == kTrial) {
+      sqp_eval_trial<R>(m, c, T.tp.EaR, w, s);
+      const int r = sqp_trial_result<R>(c, w, s);
+      if (r == 0) {
+        phase = kCheck;
+      } else if (r == 1) {
+        nmpc_apply<R>(m, c, w, T, s.info);
+        phase = kSample;
+      }
     }
-    plant_interval<R>(m, tp, j, i, F, n);
-    F_prev = F;
   }
-  out.phi = phi / (double)(K + 1);
-  return out;
 }
 
 }  // namespace mc

@@ -36,6 +36,7 @@ struct DevModel {
 struct DevCtrl {
   int kind, precision, N, n_rk4;
   int sqp_max_it, ls_max, qp_solver, ip_max_it;
+  int N_min, it_min;   // > 0: per-trajectory N in [N_min, N], limit in [it_min, sqp_max_it]
   double u_min, u_max, kP, kI, kaw, Qz, P0, sqp_tol, ip_tol, u_scale, x_scale;
   double Fconv;        // OCP input unit -> L/s
   double vmin, vmax;   // input bounds in OCP units
@@ -46,15 +47,24 @@ struct DevCtrl {
 // 32x32->64-bit products whose high halves are xored with the other counter
 // words and the round key; the key advances by two Weyl constants per round.
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+MC_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+// (host and device: the host uses it to order trajectories by their horizon)
+MC_HD uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     if (r) {
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
   }
   return c;
@@ -111,11 +121,27 @@ __device__ __forceinline__ R meas_noise(const DevModel& m, uint32_t j, uint32_t 
 
 struct TrajParams {
   double EaR, t_d, dTin;
+  int N, max_it;   // horizon and SQP iteration limit of this trajectory's OCPs
 };
 
-// Time and sign of the T_in step (uniform on [t0, tf)) and the lognormal E_a/R.
-__device__ __forceinline__ TrajParams traj_params(const DevModel& m, uint32_t j) {
+// Per-trajectory horizon and SQP iteration limit: uniform integers from the
+// words of counter (2, j, 3, 0) when the controller gives ranges.
+MC_HD void traj_horizon(const DevCtrl& c, uint32_t key0, uint32_t key1, uint32_t j, int& N,
+                        int& max_it) {
+  N = c.N;
+  max_it = c.sqp_max_it;
+  if (c.N_min <= 0 && c.it_min <= 0) return;
+  const uint4 w = philox4x32_10(make_uint4(2u, j, 3u, 0u), key0, key1);
+  if (c.N_min > 0) N = c.N_min + (int)(w.x % (uint32_t)(c.N - c.N_min + 1));
+  if (c.it_min > 0) max_it = c.it_min + (int)(w.y % (uint32_t)(c.sqp_max_it - c.it_min + 1));
+}
+
+// Time and sign of the T_in step (uniform on [t0, tf)), the lognormal E_a/R,
+// and the OCP horizon and iteration limit.
+__device__ __forceinline__ TrajParams traj_params(const DevModel& m, const DevCtrl& c,
+                                                  uint32_t j) {
   TrajParams p;
+  traj_horizon(c, m.key0, m.key1, j, p.N, p.max_it);
   const uint4 w = philox4x32_10(make_uint4(0u, j, 3u, 0u), m.key0, m.key1);
   const double tf = m.t0 + (double)m.n_steps * m.Ts;
   p.t_d = m.t0 + u52(w.x, w.y) * (tf - m.t0);

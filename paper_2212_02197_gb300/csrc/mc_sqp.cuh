@@ -1,10 +1,20 @@
 // mc_sqp.cuh -- the NMPC regulator of Sec. III-B solved by the SQP of Sec. IV,
-// and one whole NMPC closed-loop trajectory (Sec. VII), per thread.
+// per thread.
 //
 // NLP (Eq. OCP_NLP) in scaled variables: OCP state x = n_T / x_scale, OCP
 // input v with flow F = v Fconv; decision vector [v_0, x_1, ..., v_{N-1}, x_N];
 // constraints g_k = F_k - x_{k+1}; Lagrangian
 //   L = f - lam^T g - pil^T (v - v_min) - piu^T (v_max - v).
+//
+// The SQP is written as resumable phases so that a persistent kernel can run
+// each lane's SQP at its own pace while the warp's lanes share the expensive
+// shooting evaluations (see mc_closedloop.cuh):
+//   sqp_start          W = I, first evaluation at the warm start
+//   sqp_check          block BFGS, the scaled KKT test, the QP, the merit
+//                      slope, and the first trial point
+//   sqp_eval_trial     shooting at the trial point (the dominant cost)
+//   sqp_trial_result   Armijo test; accept and step, or halve the step
+// sqp_solve chains them for one OCP.
 #pragma once
 
 #include "mc_qp.cuh"
@@ -16,6 +26,15 @@ struct SqpInfo {
   double kkt_grad, kkt_eq, f;
 };
 
+// Resumable SQP state of one OCP.
+struct SqpState {
+  int N, max_it;      // horizon and iteration limit of this OCP
+  int l;              // iteration counter
+  int hv;             // halvings in the current line search
+  double f, ft, alpha, T0, DT0;
+  SqpInfo info;
+};
+
 // Shooting of all N intervals at the point (u_arr, x_arr) with sensitivities,
 // writing A_k, B_k, g_k and q_k into (a_arr, b_arr, g_arr, q_arr); returns the
 // objective f = sum_k Q_z (z_k - zbar_k)^2 T_s.  With reuse_mid the intervals
@@ -24,16 +43,17 @@ struct SqpInfo {
 // only the first and the last interval are integrated again.
 // R is the arithmetic of the RK4 integration (FP32 on the mixed-precision
 // path); the constraint residual g_k, the objective and its gradient are FP64.
+// Not inlined: the shooting loop is the hot spot, and as a function of its own
+// it gets the full register file instead of sharing it with the SQP state.
 template <class R>
-__device__ __forceinline__ double evaluate(const DevModel& m, const DevCtrl& c, double EaR,
-                                           double x0, const Ws& w, int u_arr, int x_arr,
+__device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, double EaR,
+                                           int N, const Ws& w, int u_arr, int x_arr,
                                            int a_arr, int b_arr, int g_arr, int q_arr,
                                            bool reuse_mid = false) {
-  const int N = c.N;
   const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
   const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
   double f = 0.0;
-  double xk = x0;
+  double xk = w(X, 0);
   for (int k = 0; k < N; ++k) {
     const double xn = w(x_arr, k + 1);
     if (!(reuse_mid && k >= 1 && k <= N - 2)) {
@@ -81,184 +101,248 @@ __device__ __forceinline__ void bfgs_block(int n, double& w11, double& w12, doub
   }
 }
 
-// SQP of Sec. IV for one OCP from the warm start in (U, X, LAM, PIL, PIU); the
-// set-points z-bar(t_{i+k}) are in ZB[1..N].  Returns diagnostics; the
-// solution (or the last iterate on failure) is left in U, X and the multipliers.
-// With shifted_eval the evaluation arrays hold the previous OCP's final
-// evaluation shifted by one interval (see evaluate).  R is the shooting
-// arithmetic; everything else (QP, merit, BFGS, convergence test) is FP64.
+// Trial point xi + alpha dxi (u clipped into its bounds against rounding).
+__device__ __forceinline__ void sqp_trial_point(const DevCtrl& c, const Ws& w,
+                                                const SqpState& s) {
+  for (int k = 0; k < s.N; ++k) {
+    w(UT, k) = fmin(fmax(w(U, k) + s.alpha * w(DU, k), c.vmin), c.vmax);
+    w(XT, k + 1) = w(X, k + 1) + s.alpha * w(DX, k + 1);
+  }
+}
+
+// Start an OCP from the warm start in (U, X, LAM, PIL, PIU) with x0 and the
+// set-points z-bar(t_{i+k}) in ZB[1..N]; W^[0] = I.  With shifted_eval the
+// evaluation arrays hold the previous OCP's final evaluation shifted by one
+// interval (see evaluate).
 template <class R>
-__device__ __noinline__ SqpInfo sqp_solve(const DevModel& m, const DevCtrl& c, double EaR,
-                                          double x0, const Ws& w, bool shifted_eval = false) {
-  const int N = c.N;
-  const double c1 = 1e-4, s_max = 100.0;
-  SqpInfo info{};
+__device__ __forceinline__ void sqp_start(const DevModel& m, const DevCtrl& c, double EaR,
+                                          double x0, const Ws& w, int N, int max_it,
+                                          bool shifted_eval, SqpState& s) {
+  s.N = N;
+  s.max_it = max_it;
+  s.l = 0;
+  s.hv = 0;
+  s.alpha = 0.0;
+  s.info = SqpInfo{};
   for (int k = 0; k <= N; ++k) {
     w(WXX, k) = 1.0;
     w(WXU, k) = 0.0;
     w(WUU, k) = 1.0;
   }
   w(X, 0) = x0;
-  double f = evaluate<R>(m, c, EaR, x0, w, U, X, EA, EB, EG, EQ, shifted_eval);
-  double alpha = 0.0;
-  int nqp = 0;
-  for (int l = 0;; ++l) {
-    // gradient of the Lagrangian at the current iterate and multipliers
-    double kg = 0.0, ke = 0.0, mult1 = 0.0;
-    for (int k = 0; k < N; ++k) {
-      const double lam = w(LAM, k), pil = w(PIL, k), piu = w(PIU, k);
-      mult1 += fabs(lam) + fabs(pil) + fabs(piu);
-      const double gu = -lam * w(EB, k) - pil + piu;
-      double gx;
-      if (k + 1 < N)
-        gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
-      else
-        gx = w(EQ, N) + lam;
-      if (l > 0) {
-        // damped block BFGS with s = alpha (du, dx) and
-        // y = grad L(xi^[l], .) - grad L(xi^[l-1], .) at the new multipliers
-        const double su = alpha * w(DU, k), sx = alpha * w(DX, k);
-        const double yu = gu - w(GLU, k), yx = (k > 0) ? w(GLX, k) : 0.0;
-        double w11, w12, w22;
-        if (k == 0) {
-          w11 = w(WUU, 0);
-          w12 = 0.0;
-          w22 = 0.0;
-          bfgs_block(1, w11, w12, w22, su, 0.0, yu, 0.0);
-          w(WUU, 0) = w11;
-        } else {
-          w11 = w(WXX, k);
-          w12 = w(WXU, k);
-          w22 = w(WUU, k);
-          bfgs_block(2, w11, w12, w22, sx, su, yx, yu);
-          w(WXX, k) = w11;
-          w(WXU, k) = w12;
-          w(WUU, k) = w22;
-        }
-        if (k == N - 1) {
-          double wn = w(WXX, N), d0 = 0.0, d1 = 0.0;
-          bfgs_block(1, wn, d0, d1, alpha * w(DX, N), 0.0, gx - w(GLX, N), 0.0);
-          w(WXX, N) = wn;
-        }
-        // keep the new-point x-gradient of stage k+1 for its block
-        w(GLX, k + 1) = gx - w(GLX, k + 1);
-      }
-      kg = fmax(kg, fmax(fabs(gu), fabs(gx)));
-    }
-    if (l > 0) {
-      // positive definiteness of every block, else reset all to the identity
-      bool pd = w(WUU, 0) > 0.0 && w(WXX, N) > 0.0;
-      for (int k = 1; k < N; ++k) {
-        const double a = w(WXX, k), b = w(WXU, k), d = w(WUU, k);
-        pd = pd && (a > 0.0) && (d - b * b / a > 0.0);
-      }
-      if (!pd) {
-        for (int k = 0; k <= N; ++k) {
-          w(WXX, k) = 1.0;
-          w(WXU, k) = 0.0;
-          w(WUU, k) = 1.0;
-        }
-        info.n_hess_reset++;
-      }
-    }
-    const double s_d = fmax(s_max, mult1 / (3.0 * N)) / s_max;
-    kg /= s_d;
-    for (int k = 0; k < N; ++k) ke = fmax(ke, fabs(w(EG, k)));
-    info.kkt_grad = kg;
-    info.kkt_eq = ke;
-    info.f = f;
-    if (kg <= c.sqp_tol && ke <= c.sqp_tol) {
-      info.status = 0;
-      break;
-    }
-    if (l >= c.sqp_max_it) {
-      info.status = 1;
-      break;
-    }
+  s.f = evaluate<R>(m, c, EaR, N, w, U, X, EA, EB, EG, EQ, shifted_eval);
+}
 
-    // QP subproblem at xi^[l]
-    for (int k = 0; k < N; ++k) {
-      const double u = w(U, k);
-      w(LB, k) = c.vmin - u;
-      w(UB, k) = c.vmax - u;
-    }
-    QpResult qr = (c.qp_solver == 1) ? qp_ipm(w, N, false, c.ip_max_it, c.ip_tol)
-                                     : qp_active_set(w, N, false, 10 * N + 20);
-    info.qp_iters += qr.iters;
-    if (qr.status != 0) info.qp_fail++;
-    ++nqp;
-
-    // penalty weights (sigma update) and the merit slope
-    double pen = 0.0, dfd = 0.0;
-    for (int k = 0; k < N; ++k) {
-      const double am = fabs(w(MU, k));
-      const double sg = (l == 0) ? am : fmax(am, 0.5 * (w(SIG, k) + am));
-      w(SIG, k) = sg;
-      pen += sg * fabs(w(EG, k));
-      dfd += w(EQ, k + 1) * w(DX, k + 1);
-    }
-    const double T0 = f + pen;
-    const double DT0 = dfd - pen;
-
-    // backtracking line search on the Armijo condition
-    alpha = 1.0;
-    bool accepted = false;
-    double ft = 0.0;
-    for (int hv = 0; hv <= c.ls_max; ++hv) {
-      for (int k = 0; k < N; ++k) {
-        w(UT, k) = fmin(fmax(w(U, k) + alpha * w(DU, k), c.vmin), c.vmax);
-        w(XT, k + 1) = w(X, k + 1) + alpha * w(DX, k + 1);
+// Top of an SQP iteration at xi^[l] (evaluated): damped block BFGS for l > 0,
+// the scaled KKT test of Eq. (convergence) and the iteration limit.  Returns
+// true when the OCP is finished (s.info.status set).  Otherwise solves the QP,
+// updates the l1 penalty weights, forms T(0) and its slope and prepares the
+// first trial point (alpha = 1).
+__device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, SqpState& s) {
+  const int N = s.N;
+  const double s_max = 100.0;
+  double kg = 0.0, ke = 0.0, mult1 = 0.0;
+  for (int k = 0; k < N; ++k) {
+    const double lam = w(LAM, k), pil = w(PIL, k), piu = w(PIU, k);
+    mult1 += fabs(lam) + fabs(pil) + fabs(piu);
+    const double gu = -lam * w(EB, k) - pil + piu;
+    double gx;
+    if (k + 1 < N)
+      gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
+    else
+      gx = w(EQ, N) + lam;
+    if (s.l > 0) {
+      // damped block BFGS with s = alpha (du, dx) and
+      // y = grad L(xi^[l], .) - grad L(xi^[l-1], .) at the new multipliers
+      const double su = s.alpha * w(DU, k), sx = s.alpha * w(DX, k);
+      const double yu = gu - w(GLU, k), yx = (k > 0) ? w(GLX, k) : 0.0;
+      double w11, w12, w22;
+      if (k == 0) {
+        w11 = w(WUU, 0);
+        w12 = 0.0;
+        w22 = 0.0;
+        bfgs_block(1, w11, w12, w22, su, 0.0, yu, 0.0);
+        w(WUU, 0) = w11;
+      } else {
+        w11 = w(WXX, k);
+        w12 = w(WXU, k);
+        w22 = w(WUU, k);
+        bfgs_block(2, w11, w12, w22, sx, su, yx, yu);
+        w(WXX, k) = w11;
+        w(WXU, k) = w12;
+        w(WUU, k) = w22;
       }
-      ft = evaluate<R>(m, c, EaR, x0, w, UT, XT, TA, TB, TG, TQ);
-      info.ls_trials++;
-      double pt = 0.0;
-      for (int k = 0; k < N; ++k) pt += w(SIG, k) * fabs(w(TG, k));
-      if (ft + pt <= T0 + c1 * alpha * DT0) {
-        accepted = true;
-        break;
+      if (k == N - 1) {
+        double wn = w(WXX, N), d0 = 0.0, d1 = 0.0;
+        bfgs_block(1, wn, d0, d1, s.alpha * w(DX, N), 0.0, gx - w(GLX, N), 0.0);
+        w(WXX, N) = wn;
       }
-      alpha *= 0.5;
+      // keep the new-point x-gradient of stage k+1 for its block
+      w(GLX, k + 1) = gx - w(GLX, k + 1);
     }
-    if (!accepted) {
-      info.status = 2;
-      break;
-    }
-
-    // step in the multipliers; old-point Lagrangian gradient at the new multipliers
-    for (int k = 0; k < N; ++k) {
-      const double lam = w(LAM, k) + alpha * (w(MU, k) - w(LAM, k));
-      const double pil = w(PIL, k) + alpha * (w(NUL, k) - w(PIL, k));
-      const double piu = w(PIU, k) + alpha * (w(NUU, k) - w(PIU, k));
-      w(LAM, k) = lam;
-      w(PIL, k) = pil;
-      w(PIU, k) = piu;
-    }
-    for (int k = 0; k < N; ++k) {
-      const double lam = w(LAM, k);
-      w(GLU, k) = -lam * w(EB, k) - w(PIL, k) + w(PIU, k);
-      double gx;
-      if (k + 1 < N)
-        gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
-      else
-        gx = w(EQ, N) + lam;
-      w(GLX, k + 1) = gx;
-    }
-    // accept the trial point and its evaluation; the step actually taken
-    // (after the bound clip) is what BFGS sees
-    for (int k = 0; k < N; ++k) {
-      const double un = w(UT, k);
-      w(DU, k) = (un - w(U, k)) / alpha;
-      w(U, k) = un;
-      w(X, k + 1) = w(XT, k + 1);
-      w(EA, k) = w(TA, k);
-      w(EB, k) = w(TB, k);
-      w(EG, k) = w(TG, k);
-      w(EQ, k + 1) = w(TQ, k + 1);
-    }
-    f = ft;
+    kg = fmax(kg, fmax(fabs(gu), fabs(gx)));
   }
-  info.iters = nqp;
-  return info;
+  if (s.l > 0) {
+    // positive definiteness of every block, else reset all to the identity
+    bool pd = w(WUU, 0) > 0.0 && w(WXX, N) > 0.0;
+    for (int k = 1; k < N; ++k) {
+      const double a = w(WXX, k), b = w(WXU, k), d = w(WUU, k);
+      pd = pd && (a > 0.0) && (d - b * b / a > 0.0);
+    }
+    if (!pd) {
+      for (int k = 0; k <= N; ++k) {
+        w(WXX, k) = 1.0;
+        w(WXU, k) = 0.0;
+        w(WUU, k) = 1.0;
+      }
+      s.info.n_hess_reset++;
+    }
+  }
+  const double s_d = fmax(s_max, mult1 / (3.0 * N)) / s_max;
+  kg /= s_d;
+  for (int k = 0; k < N; ++k) ke = fmax(ke, fabs(w(EG, k)));
+  s.info.kkt_grad = kg;
+  s.info.kkt_eq = ke;
+  s.info.f = s.f;
+  if (kg <= c.sqp_tol && ke <= c.sqp_tol) {
+    s.info.status = 0;
+    return true;
+  }
+  if (s.l >= s.max_it) {
+    s.info.status = 1;
+    return true;
+  }
+
+  // QP subproblem at xi^[l]
+  for (int k = 0; k < N; ++k) {
+    const double u = w(U, k);
+    w(LB, k) = c.vmin - u;
+    w(UB, k) = c.vmax - u;
+  }
+  const QpResult qr = (c.qp_solver == 1) ? qp_ipm(w, N, false, c.ip_max_it, c.ip_tol)
+                                         : qp_active_set(w, N, false, 10 * N + 20);
+  s.info.qp_iters += qr.iters;
+  if (qr.status != 0) s.info.qp_fail++;
+  s.info.iters++;
+
+  // penalty weights (sigma update) and the merit slope
+  double pen = 0.0, dfd = 0.0;
+  for (int k = 0; k < N; ++k) {
+    const double am = fabs(w(MU, k));
+    const double sg = (s.l == 0) ? am : fmax(am, 0.5 * (w(SIG, k) + am));
+    w(SIG, k) = sg;
+    pen += sg * fabs(w(EG, k));
+    dfd += w(EQ, k + 1) * w(DX, k + 1);
+  }
+  s.T0 = s.f + pen;
+  s.DT0 = dfd - pen;
+  s.alpha = 1.0;
+  s.hv = 0;
+  sqp_trial_point(c, w, s);
+  return false;
+}
+
+template <class R>
+__device__ __forceinline__ void sqp_eval_trial(const DevModel& m, const DevCtrl& c, double EaR,
+                                               const Ws& w, SqpState& s) {
+  s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ);
+  s.info.ls_trials++;
+}
+
+// Armijo test of the evaluated trial point.  Returns 0 when the step was
+// accepted (xi^[l+1] is current and evaluated; continue with sqp_check),
+// 1 when the line search ran out of halvings (status 2; the OCP is finished
+// at the current iterate), 2 when the step was halved (evaluate the new trial).
+__device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws& w,
+                                                     SqpState& s) {
+  const int N = s.N;
+  const double c1 = 1e-4;
+  double pt = 0.0;
+  for (int k = 0; k < N; ++k) pt += w(SIG, k) * fabs(w(TG, k));
+  if (!(s.ft + pt <= s.T0 + c1 * s.alpha * s.DT0)) {
+    if (s.hv >= c.ls_max) {
+      s.info.status = 2;
+      return 1;
+    }
+    s.hv++;
+    s.alpha *= 0.5;
+    sqp_trial_point(c, w, s);
+    return 2;
+  }
+  const double alpha = s.alpha;
+  // step in the multipliers; old-point Lagrangian gradient at the new multipliers
+  for (int k = 0; k < N; ++k) {
+    w(LAM, k) = w(LAM, k) + alpha * (w(MU, k) - w(LAM, k));
+    w(PIL, k) = w(PIL, k) + alpha * (w(NUL, k) - w(PIL, k));
+    w(PIU, k) = w(PIU, k) + alpha * (w(NUU, k) - w(PIU, k));
+  }
+  for (int k = 0; k < N; ++k) {
+    const double lam = w(LAM, k);
+    w(GLU, k) = -lam * w(EB, k) - w(PIL, k) + w(PIU, k);
+    double gx;
+    if (k + 1 < N)
+      gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
+    else
+      gx = w(EQ, N) + lam;
+    w(GLX, k + 1) = gx;
+  }
+  // accept the trial point and its evaluation; the step actually taken
+  // (after the bound clip) is what BFGS sees
+  for (int k = 0; k < N; ++k) {
+    const double un = w(UT, k);
+    w(DU, k) = (un - w(U, k)) / alpha;
+    w(U, k) = un;
+    w(X, k + 1) = w(XT, k + 1);
+    w(EA, k) = w(TA, k);
+    w(EB, k) = w(TB, k);
+    w(EG, k) = w(TG, k);
+    w(EQ, k + 1) = w(TQ, k + 1);
+  }
+  s.f = s.ft;
+  s.l++;
+  return 0;
+}
+
+// Code placement.  On the mixed-precision path the FP32 shooting is cheap and
+// the FP64 phases dominate; compiled as separate functions they keep their
+// own register allocation (measured 2.2x faster on the 30k study).  On the
+// FP64 path inlining them is as fast or faster.
+__device__ __noinline__ bool sqp_check_call(const DevCtrl& c, const Ws& w, SqpState& s) {
+  return sqp_check_body(c, w, s);
+}
+__device__ __noinline__ int sqp_trial_result_call(const DevCtrl& c, const Ws& w, SqpState& s) {
+  return sqp_trial_result_body(c, w, s);
+}
+template <class R>
+__device__ __forceinline__ bool sqp_check(const DevCtrl& c, const Ws& w, SqpState& s) {
+  if constexpr (sizeof(R) == 4) return sqp_check_call(c, w, s);
+  else return sqp_check_body(c, w, s);
+}
+template <class R>
+__device__ __forceinline__ int sqp_trial_result(const DevCtrl& c, const Ws& w, SqpState& s) {
+  if constexpr (sizeof(R) == 4) return sqp_trial_result_call(c, w, s);
+  else return sqp_trial_result_body(c, w, s);
+}
+
+// SQP of Sec. IV for one OCP, all phases in sequence.  Returns diagnostics;
+// the solution (or the last iterate on failure) is left in U, X and the
+// multipliers.  N and max_it default to the controller's.
+template <class R>
+__device__ __noinline__ SqpInfo sqp_solve(const DevModel& m, const DevCtrl& c, double EaR,
+                                          double x0, const Ws& w, bool shifted_eval = false,
+                                          int N = 0, int max_it = -1) {
+  SqpState s;
+  sqp_start<R>(m, c, EaR, x0, w, N > 0 ? N : c.N, max_it >= 0 ? max_it : c.sqp_max_it,
+               shifted_eval, s);
+  while (!sqp_check<R>(c, w, s)) {
+    int r;
+    do {
+      sqp_eval_trial<R>(m, c, EaR, w, s);
+      r = sqp_trial_result<R>(c, w, s);
+    } while (r == 2);
+    if (r == 1) break;
+  }
+  return s.info;
 }
 
 }  // namespace mc

@@ -28,6 +28,7 @@ MC_WARN_NONFINITE = 100
 QP_SOLVERS = {"active_set": 0, "ipm": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 KINDS = {"nmpc": 0, "pi": 1}
+SCHEDULES = {"static": 0, "persistent": 1}
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -50,7 +51,8 @@ class McController(C.Structure):
                 ("Qz", C.c_double), ("P0", C.c_double), ("sqp_max_it", C.c_int32),
                 ("ls_max", C.c_int32), ("sqp_tol", C.c_double), ("qp_solver", C.c_int32),
                 ("ip_max_it", C.c_int32), ("ip_tol", C.c_double), ("u_scale", C.c_double),
-                ("x_scale", C.c_double)]
+                ("x_scale", C.c_double), ("N_min", C.c_int32), ("sqp_max_it_min", C.c_int32),
+                ("schedule", C.c_int32), ("threads_per_sm", C.c_int32)]
 
 
 class McStats(C.Structure):
@@ -109,6 +111,10 @@ def lib():
             L.mc_reduce_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                             C.c_double, C.c_double, C.c_void_p,
                                             C.POINTER(McStats)]
+            L.mc_set_graph.argtypes = [H, C.c_int]
+            L.mc_autotune.argtypes = [H, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
+            for f in ("mc_set_graph", "mc_autotune"):
+                getattr(L, f).restype = C.c_int
             for f in ("mc_create", "mc_set_histogram", "mc_run", "mc_run_range", "mc_stats",
                       "mc_copy_phi", "mc_copy_counters", "mc_sync", "mc_philox", "mc_noise",
                       "mc_qp_solve_batch", "mc_ocp_solve_batch", "mc_reduce_noalloc"):
@@ -158,6 +164,10 @@ def make_ctrl(cd: dict) -> McController:
     c.qp_solver = QP_SOLVERS[cd.get("qp_solver", "active_set")]
     c.ip_max_it = int(cd.get("ip_max_it", 60))
     c.ip_tol = float(cd.get("ip_tol", 1e-14))
+    c.N_min = int(cd.get("N_min", 0))
+    c.sqp_max_it_min = int(cd.get("sqp_max_it_min", 0))
+    c.schedule = SCHEDULES[cd.get("schedule", "static")]
+    c.threads_per_sm = int(cd.get("threads_per_sm", 0))
     return c
 
 
@@ -200,6 +210,17 @@ class MonteCarlo:
 
     def set_histogram(self, n_bins: int, lo: float = 0.0, hi: float = 0.0):
         _check(lib().mc_set_histogram(self._h, n_bins, lo, hi), self._h)
+
+    def set_graph(self, on: bool = True):
+        """Replay each range's launches from a captured CUDA graph."""
+        _check(lib().mc_set_graph(self._h, 1 if on else 0), self._h)
+
+    def autotune(self, probe_steps: int = 8, stream=None) -> int:
+        """Resident threads per SM of the persistent schedule, chosen by timing."""
+        tps = C.c_int32()
+        _check(lib().mc_autotune(self._h, probe_steps, _stream_ptr(stream), C.byref(tps)),
+               self._h)
+        return tps.value
 
     def run(self, stream=None, j0: int = 0, j1: int | None = None):
         j1 = self.n_sims if j1 is None else j1

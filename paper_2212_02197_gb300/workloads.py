@@ -67,7 +67,9 @@ def model(n_steps: int, Ts: float = 0.5, n_em: int = 10, Ea_logsd: float = 0.0,
 def nmpc(N: int = 20, u_max: float = 800.0, precision: str = "fp64") -> dict:
     """NMPC settings of Sec. VII-A (N_c = 5 RK4 steps, Q_z = 1, P_{-1|-1} = 1e-6).
 
-    Mixed precision shoots in FP32, whose rounding (about 1e-7 of the RK4
+    FP64 runs the persistent schedule (lanes share the line-search shooting
+    while each advances its own SQP); mixed precision, where the FP64 phases
+    dominate, runs the static one.  Mixed precision shoots in FP32, whose rounding (about 1e-7 of the RK4
     increments) sets a floor under the merit function; its SQP stops at
     1e-3 on the scaled KKT test or after 3 step halvings that find no
     decrease, and is accepted statistically against FP64."""
@@ -76,7 +78,7 @@ def nmpc(N: int = 20, u_max: float = 800.0, precision: str = "fp64") -> dict:
                 ls_max=3 if mixed else 30, u_min=0.0, u_max=float(u_max), kP=-1e-3, kI=-1e-4,
                 kaw=-1e-1, Qz=1.0, P0=1e-6, sqp_tol=1e-3 if mixed else 1e-5,
                 u_scale=float(u_max), x_scale=CSTR["V"], qp_solver="active_set", ip_max_it=60,
-                ip_tol=1e-14)
+                ip_tol=1e-14, schedule="static" if mixed else "persistent")
 
 
 def pi(u_max: float = 800.0, precision: str = "fp64") -> dict:
@@ -101,6 +103,12 @@ WORKLOADS = {
     "cstr_100k_x240_N30_mixed": dict(model=model(240, Ea_logsd=0.02),
                                      nmpc=nmpc(30, precision="mixed"), pi=None,
                                      n_traj=100000, seed=SEED),
+    # uneven batches: 262,144 trajectories, 120 steps, horizon uniform on 10..40 and
+    # SQP iteration limit uniform on 5..30 per trajectory, persistent schedule
+    "cstr_262k_x120_N10to40_uneven": dict(
+        model=model(120),
+        nmpc=dict(nmpc(40), N_min=10, sqp_max_it=30, sqp_max_it_min=5, schedule="persistent"),
+        pi=None, n_traj=262144, seed=SEED),
     # the paper's own setting (Sec. VII-A): T_s = 1 s, N_s = 20, N = 60, 600 steps
     "cstr_paper_30k_x600_N60": dict(model=model(600, Ts=1.0, n_em=20,
                                                 schedule=SCHEDULE_PAPER),

@@ -293,3 +293,83 @@ def test_ipm_closed_loop_matches_oracle():
     ref = oracle.run(m, c, w["seed"], 0, 16)
     compare_phi(h.phi(), ref, h.counters(), 1e-6)
     h.close()
+
+
+# ------------------------------------------------------------------ schedules
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_schedule_is_bit_identical_to_static(precision):
+    """The persistent per-lane state machine runs the same arithmetic per
+    trajectory as the static schedule."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=40)
+    base = dict(w["nmpc"], precision=precision)
+    if precision == "mixed":
+        base.update(sqp_tol=1e-3, ls_max=3)
+    out = {}
+    for sched, tps in (("static", 0), ("persistent", 0), ("persistent", 1)):
+        h = mc.MonteCarlo(m, dict(base, schedule=sched, threads_per_sm=tps), 200, w["seed"])
+        h.run()
+        h.sync()
+        out[(sched, tps)] = (h.phi(), h.counters())
+        h.close()
+    ref_phi, ref_cnt = out[("static", 0)]
+    for key in (("persistent", 0), ("persistent", 1)):
+        phi, cnt = out[key]
+        assert np.array_equal(phi, ref_phi), key
+        for k in ref_cnt:
+            assert np.array_equal(cnt[k], ref_cnt[k]), (key, k)
+
+
+def test_uneven_batch_matches_oracle():
+    """Per-trajectory horizons 10..40 and SQP limits 5..30 (persistent
+    schedule, queue ordered by horizon) against the oracle."""
+    w = W.get("cstr_262k_x120_N10to40_uneven")
+    m = dict(w["model"], n_steps=30)
+    n = 96
+    h = mc.MonteCarlo(m, w["nmpc"], n, w["seed"])
+    h.run()
+    st = h.stats(timeout_ms=600000)
+    phi, cnt = h.phi(), h.counters()
+    h.close()
+    ref = oracle.run(m, w["nmpc"], w["seed"], 0, n)
+    compare_phi(phi, ref, cnt, 1e-6)
+    assert st["n_ocp"] == n * 30
+    # the same trajectories through the static schedule, bit for bit
+    hs = mc.MonteCarlo(m, dict(w["nmpc"], schedule="static"), n, w["seed"])
+    hs.run()
+    hs.sync()
+    assert np.array_equal(hs.phi(), phi)
+    hs.close()
+
+
+def test_graph_replay_and_autotune_keep_results():
+    """CUDA-graph replay of a captured run and an autotuned persistent
+    schedule give the same per-trajectory results as a direct launch."""
+    import torch
+
+    w = W.get("cstr_262k_x120_N10to40_uneven")
+    m = dict(w["model"], n_steps=16)
+    n = 300
+    ref = mc.MonteCarlo(m, w["nmpc"], n, w["seed"])
+    ref.run()
+    ref.sync()
+    phi0, cnt0 = ref.phi(), ref.counters()
+    ref.close()
+    s = torch.cuda.Stream()
+    h = mc.MonteCarlo(m, w["nmpc"], n, w["seed"])
+    tps = h.autotune(probe_steps=3, stream=s)
+    assert tps in (32, 64, 96, 128, 160, 192, 256, 384, 512)
+    h.set_graph(True)
+    for _ in range(2):          # capture, then replay
+        h.run(stream=s)
+        st = h.stats(timeout_ms=600000)
+        assert np.array_equal(h.phi(), phi0)
+        cnt = h.counters()
+        for k in cnt0:
+            assert np.array_equal(cnt[k], cnt0[k])
+        assert st["n_traj"] == n
+    h.run(stream=s, j0=10, j1=50)   # another range gets its own graph
+    h.sync()
+    assert np.array_equal(h.phi()[10:50], phi0[10:50])
+    h.close()

@@ -111,3 +111,27 @@ def test_degenerate_filter_is_reported_not_hidden():
     m["meas_sd"] = 0.0
     r = oracle.traj(m, w["nmpc"], w["seed"], 0)
     assert r["nonfinite"] == 1 and np.isnan(r["phi"])
+
+
+def test_uneven_horizon_draw():
+    """Uneven batches: the horizon is uniform on N_min..N and the SQP limit on
+    sqp_max_it_min..sqp_max_it, independently per trajectory."""
+    c = W.get("cstr_262k_x120_N10to40_uneven")["nmpc"]
+    Ns, its = zip(*[oracle.traj_horizon(c, 9, j) for j in range(6200)])
+    Ns, its = np.array(Ns), np.array(its)
+    assert Ns.min() == 10 and Ns.max() == 40 and its.min() == 5 and its.max() == 30
+    cnt = np.bincount(Ns - 10, minlength=31)
+    assert np.all(np.abs(cnt - 200) < 5 * np.sqrt(200))
+    assert abs(np.corrcoef(Ns, its)[0, 1]) < 0.05
+    c_fixed = W.nmpc(20)
+    assert oracle.traj_horizon(c_fixed, 9, 5) == (20, 100)
+
+
+def test_uneven_trajectory_uses_its_horizon():
+    """A trajectory's OCPs use its own iteration limit: with a limit of 5 no OCP
+    takes more than 5 QPs."""
+    w = W.get("cstr_262k_x120_N10to40_uneven")
+    m = dict(w["model"], n_steps=20)
+    c = dict(w["nmpc"], sqp_max_it=5, sqp_max_it_min=5)
+    r = oracle.run(m, c, w["seed"], 0, 6)
+    assert np.all(r["sqp_iters"] <= 5 * 20)
