@@ -20,7 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRC = ["or_random.c", "or_model.c", "or_sqp.c", "or_closedloop.c"]
+_SRC = ["or_random.c", "or_model.c", "or_sqp.c", "or_closedloop.c", "or_grad.c"]
 MAX_SP = 16
 MAX_N = 64
 
@@ -126,6 +126,11 @@ def lib():
                                   C.POINTER(TrajOut), _dp]
             L.or_run.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64, C.c_int64,
                                  C.c_int64, C.c_int, C.POINTER(TrajOut)]
+            L.or_pi_phi_cs.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64,
+                                       C.c_int64, C.c_int, C.c_double, _dp]
+            L.or_pi_phi_cs.restype = C.c_double
+            L.or_pi_grad_run.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64,
+                                         C.c_int64, C.c_int64, C.c_int, _dp, _dp]
             _lib = L
     return _lib
 
@@ -188,6 +193,30 @@ def run(model: dict, ctrl: dict, seed: int, j0: int, j1: int, threads: int | Non
     for f in TRAJ_FIELDS:
         res[f] = np.array([getattr(out[i], f) for i in range(n)])
     return res
+
+
+def pi_grad(model: dict, ctrl: dict, seed: int, j0: int, j1: int, threads: int | None = None):
+    """Phi_j and dPhi_j/d(k_P, k_I, k_aw) of PI trajectories j0..j1-1 by complex-step
+    differentiation; returns (phi[n], dphi[n, 3])."""
+    L = lib()
+    m, c = make_model(model), make_ctrl(dict(ctrl, kind="pi"))
+    n = j1 - j0
+    phi = np.zeros(max(n, 1))
+    dphi = np.zeros((max(n, 1), 3))
+    if threads is None:
+        threads = os.cpu_count() or 1
+    if n > 0:
+        L.or_pi_grad_run(C.byref(m), C.byref(c), seed, j0, j1, int(threads), _p(phi), _p(dphi))
+    return phi[:n], dphi[:n]
+
+
+def pi_phi_cs(model: dict, ctrl: dict, seed: int, j: int, which: int, h: float):
+    """(Phi_j, Im Phi_j(k + i h) / h) for gain `which` (0 k_P, 1 k_I, 2 k_aw)."""
+    L = lib()
+    m, c = make_model(model), make_ctrl(dict(ctrl, kind="pi"))
+    d = C.c_double()
+    phi = L.or_pi_phi_cs(C.byref(m), C.byref(c), seed, j, which, h, C.byref(d))
+    return phi, d.value
 
 
 def traj(model: dict, ctrl: dict, seed: int, j: int, with_trace: bool = False):

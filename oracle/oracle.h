@@ -158,6 +158,16 @@ void or_traj(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j,
 void or_run(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j0,
             int64_t j1, int n_threads, or_traj_out* out);
 
+/* ---- derivatives of Phi_j with respect to the PI gains (or_grad.c) ---- */
+/* Complex-step derivative of Phi_j with respect to gain `which` (0 = k_P,
+ * 1 = k_I, 2 = k_aw), step h_cs (imaginary); returns Phi_j, *dphi = dPhi_j/dk. */
+double or_pi_phi_cs(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j,
+                    int which, double h_cs, double* dphi);
+/* phi[j - j0] and dphi[3 (j - j0) + q] for q = k_P, k_I, k_aw, on n_threads
+ * host threads (h_cs = 1e-20 |k|). */
+void or_pi_grad_run(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j0,
+                    int64_t j1, int n_threads, double* phi, double* dphi);
+
 #ifdef __cplusplus
 }
 #endif
