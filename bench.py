@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     # smaller cases of the same workload, for profiling captures
     ap.add_argument("--n-traj", type=int, default=None)
     ap.add_argument("--n-steps", type=int, default=None)
@@ -359,6 +360,52 @@ def main():
         h32.close()
         h32p.close()
 
+    # gradient of mean Phi of the PI study with respect to (k_P, k_I, k_aw):
+    # forward sweep with checkpoints every 20 samples and the discrete adjoint,
+    # timed like the study; checked against central differences (h = 1e-5 of
+    # each gain) of the GPU's own mean Phi
+    grad = None
+    if not args.no_grad and h_p is not None and w["pi"]["precision"] == "fp64":
+        ck = 20
+        for _ in range(max(1, args.warmup)):
+            h_p.pi_grad(ck, stream, j0, j1)
+        evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        for a, b in evg:
+            flush.zero_()
+            a.record(stream)
+            h_p.pi_grad(ck, stream, j0, j1)
+            b.record(stream)
+        barrier()
+        g_ms = statistics.mean(a.elapsed_time(b) for a, b in evg)
+        gm = h_p.grad_mean()
+        g_phi = h_p.stats()["phi_mean"]
+        cp = w["pi"]
+        fd = []
+        for q, k in enumerate(("kP", "kI", "kaw")):
+            dk = 1e-5 * abs(cp[k])
+            m2 = []
+            for sgn in (1, -1):
+                g = {kk: cp[kk] for kk in ("kP", "kI", "kaw")}
+                g[k] += sgn * dk
+                h_p.set_pi_gains(g["kP"], g["kI"], g["kaw"])
+                h_p.run(stream, j0, j1)
+                m2.append(h_p.stats()["phi_mean"])
+            fd.append((m2[0] - m2[1]) / (2 * dk))
+        h_p.set_pi_gains(cp["kP"], cp["kI"], cp["kaw"])
+        h_p.run(stream, j0, j1)
+        if world > 1:
+            t = torch.tensor([g_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            g_ms = float(t.item())
+        grad = {"what": "d mean Phi / d(k_P, k_I, k_aw) of the PI study, discrete adjoint",
+                "checkpoint_every": ck, "value": world * T / (g_ms / 1e3),
+                "unit": "trajectories/s (forward + adjoint)", "ms_per_step": g_ms,
+                "phi_mean": g_phi, "grad_mean": gm.tolist(), "fd_h_rel": 1e-5,
+                "fd_grad_mean": fd,
+                "fd_rel_err": [abs(f / g - 1.0) if g != 0 else None for f, g in zip(fd, gm)]}
+
     # end to end through the C ABI with host buffers: create (config h2d),
     # run, stats and Phi copied back to host, destroy
     e2e_ms = []
@@ -418,6 +465,8 @@ def main():
             line["phi"].update(pi_mean=st_pall["phi_mean"], pi_var=st_pall["phi_var"])
         if mixed is not None:
             line["mixed"] = mixed
+        if grad is not None:
+            line["pi_grad"] = grad
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

@@ -200,6 +200,44 @@ const char* mc_status_str(mc_status s);
 const char* mc_last_error(const mc_handle* h);
 
 /* ---------------------------------------------------------------------------
+ * Gradients of the PI study.  The paper proposes the Monte Carlo study as a
+ * tool for tuning the controller (Sec. VIII); these calls give the derivative
+ * of the performance index Phi_j, Eq. (Phi), with respect to the gains of the
+ * PI law, Eq. (PI), by a discrete adjoint (reverse mode) of the simulated
+ * closed loop, so that mean Phi can be minimised by gradient methods.  The
+ * derivative is that of the discrete simulation the library runs (Euler-
+ * Maruyama substeps, Philox noise fixed by seed and trajectory index); where
+ * the input clip of Eq. (PI) saturates, the derivative through it is zero.
+ * ------------------------------------------------------------------------- */
+
+/* Replace the gains (k_P, k_I, k_aw; units as in mc_controller_t) of a PI
+ * handle.  MC_EINVAL for an NMPC handle or non-finite gains. */
+mc_status mc_set_pi_gains(mc_handle* h, double kP, double kI, double kaw);
+
+/* Run trajectories j0 .. j1-1 of a PI handle (FP64 only) forward and
+ * backward on cuda_stream, asynchronously.  Writes what mc_run_range writes
+ * (Phi_j, the counters, the statistics for mc_stats) and, per trajectory,
+ * dPhi_j/d(k_P, k_I, k_aw).  The forward sweep stores the plant state and
+ * the integral state every checkpoint_every samples (1..32); the backward
+ * sweep recomputes each segment from its checkpoint.  The first call
+ * allocates the gradient buffers (24 B per trajectory) and the checkpoints
+ * (32 B per trajectory and checkpoint), kept until mc_destroy.
+ * MC_EINVAL for an NMPC or mixed-precision handle, a bad range or
+ * checkpoint interval, or n_em > 32; MC_ENOMEM if the buffers cannot be had. */
+mc_status mc_pi_grad(mc_handle* h, int64_t j0, int64_t j1, int32_t checkpoint_every,
+                     void* cuda_stream);
+
+/* Wait for the last mc_pi_grad (as mc_stats does) and write the mean of
+ * dPhi_j/d(k_P, k_I, k_aw) over its trajectories with a finite Phi_j to out
+ * (3 doubles, host).  MC_ENOTRUN before any mc_pi_grad; MC_WARN_NONFINITE
+ * (out still written) when some trajectory was non-finite. */
+mc_status mc_grad_mean(mc_handle* h, double out[3], int64_t timeout_ms);
+
+/* Copy dPhi_j/d(k_P, k_I, k_aw) of trajectories j0 .. j0+n-1, row-major
+ * n x 3 doubles (NaN rows for non-finite trajectories). */
+mc_status mc_copy_grad(mc_handle* h, int64_t j0, int64_t n, double* dst, int dst_is_device);
+
+/* ---------------------------------------------------------------------------
  * Building blocks of the hot path, exposed for batched use and for testing
  * each step against an independent implementation.  All pointers are host
  * memory; the call copies in, runs one kernel and copies out (blocking).
@@ -217,6 +255,11 @@ mc_status mc_philox(const uint32_t* ctr_host, const uint32_t key[2], int64_t n,
  * transform of the same Philox words. */
 mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t precision,
                    double* out_host, double* meas_host);
+
+/* The FP64 exponential every rate-law evaluation of the simulation uses
+ * (k = k0 exp(-(E_a/R)/T), Eq. (CSTR)): y = e^x for n values, host arrays.
+ * Tang's table-driven method; within about 1 ulp of the exact value. */
+mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host);
 
 /* Solve n structured QP subproblems, Eq. (QP-subproblem)/(nlpsqp_qp), with the
  * selected solver.  Inputs are n x N (A, B, b, r, lb, ub) and n x (N+1)

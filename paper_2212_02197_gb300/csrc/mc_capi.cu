@@ -19,6 +19,7 @@
 
 #include "../../include/mc.h"
 #include "mc_closedloop.cuh"
+#include "mc_grad.cuh"
 
 namespace mc {
 
@@ -215,6 +216,11 @@ __global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1
   if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
 }
 
+__global__ void k_exp(const double* __restrict__ x, int64_t n, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = expr(x[i]);
+}
+
 __global__ void k_noise(DevModel m, uint32_t j, int64_t k0, int64_t nk, int precision,
                         double* __restrict__ out, double* __restrict__ meas) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,6 +370,12 @@ struct mc_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool ran = false;
   int64_t last_j0 = 0, last_j1 = 0;
+  // gradients of the PI study (allocated by the first mc_pi_grad)
+  double* dphi = nullptr;      // n_sims x 3
+  double* ck = nullptr;        // checkpoints, 4 x n_ck x n_sims
+  int64_t ck_words = 0;
+  double* gmean = nullptr;     // mean gradient and the finite count
+  bool grad_ran = false;
   std::string err;
 };
 
@@ -512,6 +524,9 @@ void mc_destroy(mc_handle* h) {
   cudaFree(h->dstats);
   cudaFree(h->order);
   cudaFree(h->next);
+  cudaFree(h->dphi);
+  cudaFree(h->ck);
+  cudaFree(h->gmean);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -829,6 +844,95 @@ mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
   return MC_OK;
 }
 
+// ------------------------------------------------ gradients of the PI study
+
+mc_status mc_set_pi_gains(mc_handle* h, double kP, double kI, double kaw) {
+  if (!h) return MC_EINVAL;
+  if (h->c.kind != MC_CTRL_PI) return fail(h, MC_EINVAL, "mc_set_pi_gains needs a PI handle");
+  if (!std::isfinite(kP) || !std::isfinite(kI) || !std::isfinite(kaw))
+    return fail(h, MC_EINVAL, "the gains must be finite");
+  h->c.kP = kP;
+  h->c.kI = kI;
+  h->c.kaw = kaw;
+  drop_graphs(h);  // captured launches hold the old gains
+  return MC_OK;
+}
+
+mc_status mc_pi_grad(mc_handle* h, int64_t j0, int64_t j1, int32_t checkpoint_every,
+                     void* cuda_stream) {
+  if (!h) return MC_EINVAL;
+  if (h->c.kind != MC_CTRL_PI) return fail(h, MC_EINVAL, "mc_pi_grad needs a PI handle");
+  if (h->c.precision != MC_FP64) return fail(h, MC_EINVAL, "mc_pi_grad runs in FP64 only");
+  if (j0 < 0 || j1 < j0 || j1 > h->n_sims) return fail(h, MC_EINVAL, "bad trajectory range");
+  if (checkpoint_every < 1 || checkpoint_every > kGradMaxSeg)
+    return fail(h, MC_EINVAL, "checkpoint_every must be 1..32");
+  if (h->m.n_em > kGradMaxEm) return fail(h, MC_EINVAL, "the gradient supports n_em <= 32");
+  const int K = h->m.n_steps;
+  const int n_ck = K > 0 ? (K + checkpoint_every - 1) / checkpoint_every : 1;
+  const int64_t words = (int64_t)4 * n_ck * (h->n_sims > 0 ? h->n_sims : 1);
+  if (!h->dphi) {
+    if (cudaMalloc((void**)&h->dphi, sizeof(double) * 3 * (h->n_sims > 0 ? h->n_sims : 1)) !=
+            cudaSuccess ||
+        cudaMalloc((void**)&h->gmean, sizeof(double) * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MC_ENOMEM, "cudaMalloc failed for the gradient buffers");
+    }
+  }
+  if (words > h->ck_words) {
+    cudaFree(h->ck);
+    h->ck = nullptr;
+    h->ck_words = 0;
+    if (cudaMalloc((void**)&h->ck, sizeof(double) * words) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MC_ENOMEM, "cudaMalloc failed for the checkpoints");
+    }
+    h->ck_words = words;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  MC_CUDA(h, cudaEventRecord(h->ev0, st));
+  if (j1 > j0) {
+    const int64_t blocks = (j1 - j0 + 127) / 128;
+    k_pi_grad<<<(unsigned)blocks, 128, 0, st>>>(h->m, h->c, j0, j1, checkpoint_every, n_ck, h->ck,
+                                                h->n_sims, h->phi, h->cnt, h->dphi);
+    MC_CUDA(h, cudaGetLastError());
+  }
+  k_grad_mean<<<1, kGradThreads, 0, st>>>(h->phi, h->dphi, j0, j1, h->gmean);
+  MC_CUDA(h, cudaGetLastError());
+  const mc_status s = launch_stats(h, j0, j1, st);
+  if (s != MC_OK) return s;
+  MC_CUDA(h, cudaEventRecord(h->ev1, st));
+  h->ran = true;
+  h->grad_ran = true;
+  h->last_j0 = j0;
+  h->last_j1 = j1;
+  return MC_OK;
+}
+
+mc_status mc_grad_mean(mc_handle* h, double out[3], int64_t timeout_ms) {
+  if (!h || !out) return MC_EINVAL;
+  if (!h->grad_ran) return fail(h, MC_ENOTRUN, "mc_pi_grad has not been called");
+  mc_status s = mc_sync(h, timeout_ms);
+  if (s != MC_OK) return s;
+  double g[4];
+  MC_CUDA(h, cudaMemcpy(g, h->gmean, sizeof(g), cudaMemcpyDeviceToHost));
+  out[0] = g[0];
+  out[1] = g[1];
+  out[2] = g[2];
+  return (g[3] < (double)(h->last_j1 - h->last_j0)) ? MC_WARN_NONFINITE : MC_OK;
+}
+
+mc_status mc_copy_grad(mc_handle* h, int64_t j0, int64_t n, double* dst, int dst_is_device) {
+  if (!h || (!dst && n > 0)) return MC_EINVAL;
+  if (!h->grad_ran) return fail(h, MC_ENOTRUN, "mc_pi_grad has not been called");
+  if (j0 < 0 || n < 0 || j0 + n > h->n_sims) return fail(h, MC_EINVAL, "bad range");
+  if (n == 0) return MC_OK;
+  mc_status s = mc_sync(h, 0);
+  if (s != MC_OK) return s;
+  MC_CUDA(h, cudaMemcpy(dst, h->dphi + 3 * j0, sizeof(double) * 3 * n,
+                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
 // ----------------------------------------------------------- building blocks
 
 mc_status mc_philox(const uint32_t* ctr_host, const uint32_t key[2], int64_t n,
@@ -871,6 +975,24 @@ mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t pre
   }
   cudaFree(d);
   cudaFree(dm);
+  return s;
+}
+
+mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host) {
+  if (n < 0 || (n > 0 && (!x_host || !out_host)))
+    return fail(nullptr, MC_EINVAL, "mc_exp_batch: bad arguments");
+  if (n == 0) return MC_OK;
+  double *dx = nullptr, *dy = nullptr;
+  mc_status s = MC_OK;
+  if (!to_dev<double>(&dx, x_host, n) || !to_dev<double>(&dy, nullptr, n)) {
+    s = fail(nullptr, MC_ENOMEM, "mc_exp_batch: allocation");
+  } else {
+    k_exp<<<(unsigned)((n + 255) / 256), 256>>>(dx, n, dy);
+    const cudaError_t e = cudaMemcpy(out_host, dy, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_exp_batch");
+  }
+  cudaFree(dx);
+  cudaFree(dy);
   return s;
 }
 

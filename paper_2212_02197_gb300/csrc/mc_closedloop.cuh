@@ -8,9 +8,10 @@
 //   nmpc_persistent  a per-lane state machine: every lane advances its own
 //                    trajectory through the cheap phases until it needs a
 //                    line-search evaluation, and the warp then shoots all
-//                    pending trial points together; finished lanes take the
-//                    next trajectory from a queue.  Same arithmetic per
-//                    trajectory, bit for bit.
+//                    pending trial points together (or, when few are
+//                    pending, each in turn with its intervals spread over the
+//                    lanes); finished lanes take the next trajectory from a
+//                    queue.  Same arithmetic per trajectory, bit for bit.
 #pragma once
 
 #include "mc_sqp.cuh"
@@ -270,9 +271,33 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       }
     }
     // the shared, expensive part: all lanes with a pending trial shoot it
-    if (!__any_sync(0xffffffffu, phase == kTrial)) break;
-    if (phase == kTrial) {
+    const unsigned tm = __ballot_sync(0xffffffffu, phase == kTrial);
+    if (!tm) break;
+    // Jointly, the warp runs the longest pending horizon once; a warp
+    // instruction costs the FP64 pipe the same whatever its active lanes.
+    // Cooperatively, each pending trial is shot in turn with its intervals
+    // spread over the 32 lanes, at ceil(N/32) intervals per lane.  Few
+    // pending trials (the tail of a warp whose other lanes have finished)
+    // take the cooperative route.
+    const int Nt = (phase == kTrial) ? s.N : 0;
+    const unsigned maxN = __reduce_max_sync(0xffffffffu, (unsigned)Nt);
+    const unsigned coop = __reduce_add_sync(0xffffffffu, (unsigned)((Nt + 31) / 32));
+    if (8u * coop <= 7u * maxN) {
+      const int lane = threadIdx.x & 31;
+      __syncwarp();  // the owners' trial points are visible to the helpers
+      for (unsigned rem = tm; rem; rem &= rem - 1u) {
+        const int o = __ffs(rem) - 1;
+        const int No = __shfl_sync(0xffffffffu, s.N, o);
+        const double EaRo = __shfl_sync(0xffffffffu, T.tp.EaR, o);
+        const Ws wo{w.p + (o - lane), w.ld, w.N1};
+        sqp_shoot_trial_coop<R>(m, c, EaRo, No, wo, lane);
+      }
+      __syncwarp();  // the helpers' A_k, B_k, g_k are visible to the owners
+      if (phase == kTrial) sqp_eval_trial_shot<R>(m, c, T.tp.EaR, w, s);
+    } else if (phase == kTrial) {
       sqp_eval_trial<R>(m, c, T.tp.EaR, w, s);
+    }
+    if (phase == kTrial) {
       const int r = sqp_trial_result<R>(c, w, s);
       if (r == 0) {
         phase = kCheck;

@@ -35,12 +35,36 @@ struct SqpState {
   SqpInfo info;
 };
 
-// Shooting of all N intervals at the point (u_arr, x_arr) with sensitivities,
-// writing A_k, B_k, g_k and q_k into (a_arr, b_arr, g_arr, q_arr); returns the
-// objective f = sum_k Q_z (z_k - zbar_k)^2 T_s.  With reuse_mid the intervals
-// 1 .. N-2 keep the A_k, B_k, g_k already in the arrays: after the receding-
-// horizon shift they are the previous OCP's values at the same (x_k, u_k), so
-// only the first and the last interval are integrated again.
+// One shooting interval with sensitivities: F_k = RK4^{N_c}(x_k, u_k) and
+// A_k = dF_k/dx_k, B_k = dF_k/du_k in the scaled variables, and the residual
+// g_k = F_k - x_{k+1}.  Not inlined: the joint loop of evaluate and the
+// cooperative shooting (one interval per lane) run this one compiled body, so
+// both give the same bits.
+template <class R>
+__device__ __noinline__ void shoot_interval(const DevModel& m, const DevCtrl& c, double EaR,
+                                            double xk, double uk, double xn, double xs,
+                                            double ixs, double& A, double& B, double& g) {
+  R Fn, a, b;
+  rk4_interval<R, true>(m, (R)EaR, c.n_rk4, (R)m.Ts, (R)(xk * xs), (R)uk, (R)c.Fconv, Fn, a,
+                        b);
+  A = (double)a;
+  B = (double)b * ixs;
+  g = (double)Fn * ixs - xn;
+}
+
+// Which intervals evaluate integrates.
+enum RkMode : int {
+  kRkAll = 0,   // every interval
+  kRkEnds = 1,  // only 0 and N-1: after the receding-horizon shift the
+                // intervals 1 .. N-2 hold the previous OCP's A_k, B_k, g_k at
+                // the same (x_k, u_k)
+  kRkNone = 2   // none: the arrays were filled by the cooperative shooting
+};
+
+// Shooting of the intervals selected by rk_mode at the point (u_arr, x_arr),
+// writing A_k, B_k, g_k into (a_arr, b_arr, g_arr) and q_k = df/dx_k into
+// q_arr; returns the objective f = sum_k Q_z (z_k - zbar_k)^2 T_s, which
+// depends on the states only.
 // R is the arithmetic of the RK4 integration (FP32 on the mixed-precision
 // path); the constraint residual g_k, the objective and its gradient are FP64.
 // Not inlined: the shooting loop is the hot spot, and as a function of its own
@@ -49,20 +73,19 @@ template <class R>
 __device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, double EaR,
                                            int N, const Ws& w, int u_arr, int x_arr,
                                            int a_arr, int b_arr, int g_arr, int q_arr,
-                                           bool reuse_mid = false) {
+                                           int rk_mode) {
   const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
   const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
   double f = 0.0;
   double xk = w(X, 0);
   for (int k = 0; k < N; ++k) {
     const double xn = w(x_arr, k + 1);
-    if (!(reuse_mid && k >= 1 && k <= N - 2)) {
-      R Fn, a, b;
-      rk4_interval<R, true>(m, (R)EaR, c.n_rk4, (R)m.Ts, (R)(xk * xs), (R)w(u_arr, k),
-                            (R)c.Fconv, Fn, a, b);
-      w(a_arr, k) = (double)a;
-      w(b_arr, k) = (double)b * ixs;
-      w(g_arr, k) = (double)Fn * ixs - xn;
+    if (rk_mode == kRkAll || (rk_mode == kRkEnds && (k == 0 || k == N - 1))) {
+      double A, B, g;
+      shoot_interval<R>(m, c, EaR, xk, w(u_arr, k), xn, xs, ixs, A, B, g);
+      w(a_arr, k) = A;
+      w(b_arr, k) = B;
+      w(g_arr, k) = g;
     }
     const double dz = xn * xs * m.iV - w(ZB, k + 1);
     f += c.Qz * dz * dz * m.Ts;
@@ -130,7 +153,7 @@ __device__ __forceinline__ void sqp_start(const DevModel& m, const DevCtrl& c, d
     w(WUU, k) = 1.0;
   }
   w(X, 0) = x0;
-  s.f = evaluate<R>(m, c, EaR, N, w, U, X, EA, EB, EG, EQ, shifted_eval);
+  s.f = evaluate<R>(m, c, EaR, N, w, U, X, EA, EB, EG, EQ, shifted_eval ? kRkEnds : kRkAll);
 }
 
 // Top of an SQP iteration at xi^[l] (evaluated): damped block BFGS for l > 0,
@@ -245,8 +268,37 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
 template <class R>
 __device__ __forceinline__ void sqp_eval_trial(const DevModel& m, const DevCtrl& c, double EaR,
                                                const Ws& w, SqpState& s) {
-  s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ);
+  s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ, kRkAll);
   s.info.ls_trials++;
+}
+
+// The same trial evaluation after the warp has shot the intervals
+// (sqp_shoot_trial_coop): only the objective and q_k are formed here.
+template <class R>
+__device__ __forceinline__ void sqp_eval_trial_shot(const DevModel& m, const DevCtrl& c,
+                                                    double EaR, const Ws& w, SqpState& s) {
+  s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ, kRkNone);
+  s.info.ls_trials++;
+}
+
+// Cooperative shooting of one lane's trial point: every lane of the warp
+// calls this with the owner's column wo, horizon No and E_a/R, and integrates
+// the intervals k = lane, lane + 32, ... in parallel with the other lanes.
+// The writes go to the owner's arrays; the caller orders them before the
+// owner reads (__syncwarp).
+template <class R>
+__device__ __forceinline__ void sqp_shoot_trial_coop(const DevModel& m, const DevCtrl& c,
+                                                     double EaRo, int No, const Ws& wo,
+                                                     int lane) {
+  const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
+  for (int k = lane; k < No; k += 32) {
+    const double xk = (k == 0) ? wo(X, 0) : wo(XT, k);
+    double A, B, g;
+    shoot_interval<R>(m, c, EaRo, xk, wo(UT, k), wo(XT, k + 1), xs, ixs, A, B, g);
+    wo(TA, k) = A;
+    wo(TB, k) = B;
+    wo(TG, k) = g;
+  }
 }
 
 // Armijo test of the evaluated trial point.  Returns 0 when the step was

@@ -113,7 +113,14 @@ def lib():
                                             C.POINTER(McStats)]
             L.mc_set_graph.argtypes = [H, C.c_int]
             L.mc_autotune.argtypes = [H, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
-            for f in ("mc_set_graph", "mc_autotune"):
+            L.mc_exp_batch.argtypes = [_dp, C.c_int64, _dp]
+            L.mc_exp_batch.restype = C.c_int
+            L.mc_set_pi_gains.argtypes = [H, C.c_double, C.c_double, C.c_double]
+            L.mc_pi_grad.argtypes = [H, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]
+            L.mc_grad_mean.argtypes = [H, _dp, C.c_int64]
+            L.mc_copy_grad.argtypes = [H, C.c_int64, C.c_int64, C.c_void_p, C.c_int]
+            for f in ("mc_set_graph", "mc_autotune", "mc_set_pi_gains", "mc_pi_grad",
+                      "mc_grad_mean", "mc_copy_grad"):
                 getattr(L, f).restype = C.c_int
             for f in ("mc_create", "mc_set_histogram", "mc_run", "mc_run_range", "mc_stats",
                       "mc_copy_phi", "mc_copy_counters", "mc_sync", "mc_philox", "mc_noise",
@@ -262,8 +269,46 @@ class MonteCarlo:
         _check(lib().mc_copy_counters(self._h, j0, n, a.ctypes.data_as(C.c_void_p), 0), self._h)
         return {k: a[:, i].copy() for i, k in enumerate(COUNTER_NAMES)}
 
+    # -- gradients of the PI study
+
+    def set_pi_gains(self, kP: float, kI: float, kaw: float):
+        _check(lib().mc_set_pi_gains(self._h, float(kP), float(kI), float(kaw)), self._h)
+
+    def pi_grad(self, checkpoint_every: int = 20, stream=None, j0: int = 0,
+                j1: int | None = None):
+        """Forward and adjoint sweeps of trajectories j0..j1-1 (asynchronous)."""
+        j1 = self.n_sims if j1 is None else j1
+        _check(lib().mc_pi_grad(self._h, j0, j1, int(checkpoint_every), _stream_ptr(stream)),
+               self._h)
+
+    def grad_mean(self, timeout_ms: int = 0) -> np.ndarray:
+        """Mean dPhi/d(k_P, k_I, k_aw) over the finite trajectories of the last pi_grad."""
+        g = np.zeros(3)
+        _check(lib().mc_grad_mean(self._h, _p(g), timeout_ms), self._h,
+               ok=(MC_OK, MC_WARN_NONFINITE))
+        return g
+
+    def grad(self, j0: int = 0, n: int | None = None, out=None):
+        """Per-trajectory dPhi_j/d(k_P, k_I, k_aw), n x 3: a numpy array, or into
+        `out` (a CUDA torch tensor of float64, copied device to device)."""
+        n = self.n_sims - j0 if n is None else n
+        if out is not None:
+            _check(lib().mc_copy_grad(self._h, j0, n, C.c_void_p(out.data_ptr()), 1), self._h)
+            return out
+        a = np.empty((n, 3), dtype=np.float64)
+        _check(lib().mc_copy_grad(self._h, j0, n, a.ctypes.data_as(C.c_void_p), 0), self._h)
+        return a
+
 
 # ------------------------------------------------------------------ building blocks
+
+def exp_batch(x):
+    """The device FP64 exponential of the rate law, elementwise on x."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.empty_like(x)
+    _check(lib().mc_exp_batch(_p(x), len(x), _p(y)))
+    return y
+
 
 def philox(ctr, key):
     """Device Philox4x32-10 of counters ctr (n x 4 uint32) under key (2 words)."""
