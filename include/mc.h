@@ -194,6 +194,18 @@ mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
  * mc_stats). */
 mc_status mc_sync(mc_handle* h, int64_t timeout_ms);
 
+/* Restrict the handle's kernels to a partition of at least n_sms SMs (a green
+ * context; the driver rounds up to its partition granularity, 8 SMs on
+ * sm_90 and later); n_sms = 0 or >= the device's SM count restores the whole
+ * GPU.  *n_sms_out (may be NULL) receives the SMs the handle now uses.  The
+ * paper measures how its study scales with CPU cores (Sec. VII-B, Fig. 2);
+ * this is the GPU's counterpart.  Runs are launched on the partition's own
+ * stream, ordered after the caller's stream and joined back into it, so the
+ * stream semantics of mc_run_range are unchanged; CUDA-graph replay is not
+ * used while a partition is set.  Waits for the device to be idle.
+ * MC_ECUDA if the driver has no green contexts. */
+mc_status mc_set_sm_partition(mc_handle* h, int32_t n_sms, int32_t* n_sms_out);
+
 void mc_destroy(mc_handle* h);
 const char* mc_status_str(mc_status s);
 /* last error message of a handle; NULL gives the last mc_create failure */

@@ -17,6 +17,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>  // driver types for SM partitions; entry points are resolved at run time
+
 #include "../../include/mc.h"
 #include "mc_closedloop.cuh"
 #include "mc_grad.cuh"
@@ -376,6 +378,12 @@ struct mc_handle {
   int64_t ck_words = 0;
   double* gmean = nullptr;     // mean gradient and the finite count
   bool grad_ran = false;
+  // SM partition (green context): launches go to pstream, forked from and
+  // joined back into the caller's stream
+  CUgreenCtx gctx = nullptr;
+  CUstream pstream = nullptr;
+  int part_sms = 0;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 };
 
@@ -513,6 +521,7 @@ const char* mc_last_error(const mc_handle* h) {
 }
 
 static void drop_graphs(mc_handle* h);
+static void drop_partition(mc_handle* h);
 
 void mc_destroy(mc_handle* h) {
   if (!h) return;
@@ -527,6 +536,7 @@ void mc_destroy(mc_handle* h) {
   cudaFree(h->dphi);
   cudaFree(h->ck);
   cudaFree(h->gmean);
+  drop_partition(h);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -674,14 +684,139 @@ static void drop_graphs(mc_handle* h) {
   h->graphs.clear();
 }
 
+// ---------------------------------------------------------------- SM partitions
+// Green contexts (driver API) restrict a stream's kernels to a subset of the
+// SMs.  The driver entry points are looked up through the runtime, so the
+// library does not link against libcuda.
+
+namespace {
+struct GreenApi {
+  CUresult (*dev_get)(CUdevice*, int) = nullptr;
+  CUresult (*dev_resource)(CUdevice, CUdevResource*, CUdevResourceType) = nullptr;
+  CUresult (*split)(CUdevResource*, unsigned int*, const CUdevResource*, CUdevResource*,
+                    unsigned int, unsigned int) = nullptr;
+  CUresult (*gen_desc)(CUdevResourceDesc*, CUdevResource*, unsigned int) = nullptr;
+  CUresult (*create)(CUgreenCtx*, CUdevResourceDesc, CUdevice, unsigned int) = nullptr;
+  CUresult (*destroy)(CUgreenCtx) = nullptr;
+  CUresult (*stream_create)(CUstream*, CUgreenCtx, unsigned int, int) = nullptr;
+  CUresult (*stream_destroy)(CUstream) = nullptr;
+  bool ok = false;
+};
+
+const GreenApi& green_api() {
+  static const GreenApi api = [] {
+    GreenApi a;
+    auto get = [](const char* name, void** fn) {
+      cudaDriverEntryPointQueryResult q;
+      return cudaGetDriverEntryPointByVersion(name, fn, 13000, cudaEnableDefault, &q) ==
+                 cudaSuccess &&
+             q == cudaDriverEntryPointSuccess && *fn != nullptr;
+    };
+    a.ok = get("cuDeviceGet", (void**)&a.dev_get) &&
+           get("cuDeviceGetDevResource", (void**)&a.dev_resource) &&
+           get("cuDevSmResourceSplitByCount", (void**)&a.split) &&
+           get("cuDevResourceGenerateDesc", (void**)&a.gen_desc) &&
+           get("cuGreenCtxCreate", (void**)&a.create) &&
+           get("cuGreenCtxDestroy", (void**)&a.destroy) &&
+           get("cuGreenCtxStreamCreate", (void**)&a.stream_create) &&
+           get("cuStreamDestroy", (void**)&a.stream_destroy);
+    cudaGetLastError();
+    return a;
+  }();
+  return api;
+}
+}  // namespace
+
+static void drop_partition(mc_handle* h) {
+  const GreenApi& g = green_api();
+  if (h->pstream && g.stream_destroy) g.stream_destroy(h->pstream);
+  if (h->gctx && g.destroy) g.destroy(h->gctx);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->pstream = nullptr;
+  h->gctx = nullptr;
+  h->ev_fork = h->ev_join = nullptr;
+  h->part_sms = 0;
+}
+
+// The stream the handle's kernels go to: the caller's, or the partition's
+// stream made to wait for the caller's work so far.
+static cudaStream_t fork_stream(mc_handle* h, cudaStream_t st) {
+  if (!h->pstream) return st;
+  cudaEventRecord(h->ev_fork, st);
+  cudaStreamWaitEvent((cudaStream_t)h->pstream, h->ev_fork, 0);
+  return (cudaStream_t)h->pstream;
+}
+
+// The caller's stream waits for what was launched on ls.
+static void join_stream(mc_handle* h, cudaStream_t st, cudaStream_t ls) {
+  if (ls == st) return;
+  cudaEventRecord(h->ev_join, ls);
+  cudaStreamWaitEvent(st, h->ev_join, 0);
+}
+
 extern "C" {
+
+mc_status mc_set_sm_partition(mc_handle* h, int32_t n_sms, int32_t* n_sms_out) {
+  if (!h) return MC_EINVAL;
+  if (n_sms < 0) return fail(h, MC_EINVAL, "n_sms must be >= 0");
+  MC_CUDA(h, cudaDeviceSynchronize());
+  drop_partition(h);
+  drop_graphs(h);
+  int dev = 0, sms = 0;
+  MC_CUDA(h, cudaGetDevice(&dev));
+  MC_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (n_sms == 0 || n_sms >= sms) {
+    if (n_sms_out) *n_sms_out = sms;
+    return MC_OK;
+  }
+  const GreenApi& g = green_api();
+  if (!g.ok) return fail(h, MC_ECUDA, "the driver offers no green contexts (SM partitions)");
+  auto drv = [&](CUresult r, const char* what) -> mc_status {
+    if (r == CUDA_SUCCESS) return MC_OK;
+    drop_partition(h);
+    return fail(h, MC_ECUDA, std::string(what) + " failed (CUresult " + std::to_string((int)r) +
+                                 ")");
+  };
+  CUdevice cdev;
+  mc_status s = drv(g.dev_get(&cdev, dev), "cuDeviceGet");
+  if (s != MC_OK) return s;
+  CUdevResource all, part, rest;
+  memset(&all, 0, sizeof(all));
+  memset(&part, 0, sizeof(part));
+  memset(&rest, 0, sizeof(rest));
+  if ((s = drv(g.dev_resource(cdev, &all, CU_DEV_RESOURCE_TYPE_SM), "cuDeviceGetDevResource")) !=
+      MC_OK)
+    return s;
+  unsigned int groups = 1;
+  if ((s = drv(g.split(&part, &groups, &all, &rest, 0, (unsigned)n_sms),
+               "cuDevSmResourceSplitByCount")) != MC_OK)
+    return s;
+  if (groups < 1) return fail(h, MC_EINVAL, "no SM partition of that size");
+  CUdevResourceDesc desc;
+  if ((s = drv(g.gen_desc(&desc, &part, 1), "cuDevResourceGenerateDesc")) != MC_OK) return s;
+  if ((s = drv(g.create(&h->gctx, desc, cdev, CU_GREEN_CTX_DEFAULT_STREAM), "cuGreenCtxCreate")) !=
+      MC_OK)
+    return s;
+  if ((s = drv(g.stream_create(&h->pstream, h->gctx, CU_STREAM_NON_BLOCKING, 0),
+               "cuGreenCtxStreamCreate")) != MC_OK)
+    return s;
+  if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    drop_partition(h);
+    return fail(h, MC_ECUDA, "cudaEventCreate failed");
+  }
+  h->part_sms = (int)part.sm.smCount;
+  if (n_sms_out) *n_sms_out = h->part_sms;
+  return MC_OK;
+}
 
 mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) {
   if (!h) return MC_EINVAL;
   if (j0 < 0 || j1 < j0 || j1 > h->n_sims) return fail(h, MC_EINVAL, "bad trajectory range");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   MC_CUDA(h, cudaEventRecord(h->ev0, st));
-  if (h->use_graph && st != nullptr) {
+  if (h->use_graph && st != nullptr && !h->pstream) {
     // replay the captured launches of this range, capturing them on first use
     cudaGraphExec_t exec = nullptr;
     for (const auto& g : h->graphs)
@@ -703,7 +838,9 @@ mc_status mc_run_range(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) 
     }
     MC_CUDA(h, cudaGraphLaunch(exec, st));
   } else {
-    const mc_status s = enqueue_run(h, h->m, j0, j1, h->persist_threads, st);
+    const cudaStream_t ls = fork_stream(h, st);
+    const mc_status s = enqueue_run(h, h->m, j0, j1, h->persist_threads, ls);
+    join_stream(h, st, ls);
     if (s != MC_OK) return s;
   }
   MC_CUDA(h, cudaEventRecord(h->ev1, st));
@@ -731,6 +868,7 @@ mc_status mc_autotune(mc_handle* h, int32_t probe_steps, void* cuda_stream,
   int dev = 0, sms = 152;
   MC_CUDA(h, cudaGetDevice(&dev));
   MC_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (h->part_sms > 0) sms = h->part_sms;
   DevModel probe = h->m;
   probe.n_steps = probe_steps < h->m.n_steps ? probe_steps : h->m.n_steps;
   static const int cand[] = {32, 64, 96, 128, 160, 192, 256, 384, 512};
@@ -748,7 +886,9 @@ mc_status mc_autotune(mc_handle* h, int32_t probe_steps, void* cuda_stream,
     if (!last && threads >= h->ws_ld) continue;
     const int64_t pt = threads < h->ws_ld ? threads : h->ws_ld;
     MC_CUDA(h, cudaEventRecord(a, st));
-    mc_status s = enqueue_run(h, probe, 0, h->n_sims, pt, st);
+    const cudaStream_t ls = fork_stream(h, st);
+    mc_status s = enqueue_run(h, probe, 0, h->n_sims, pt, ls);
+    join_stream(h, st, ls);
     if (s != MC_OK) return s;
     MC_CUDA(h, cudaEventRecord(b, st));
     MC_CUDA(h, cudaEventSynchronize(b));
@@ -890,15 +1030,16 @@ mc_status mc_pi_grad(mc_handle* h, int64_t j0, int64_t j1, int32_t checkpoint_ev
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   MC_CUDA(h, cudaEventRecord(h->ev0, st));
+  const cudaStream_t ls = fork_stream(h, st);
   if (j1 > j0) {
     const int64_t blocks = (j1 - j0 + 127) / 128;
-    k_pi_grad<<<(unsigned)blocks, 128, 0, st>>>(h->m, h->c, j0, j1, checkpoint_every, n_ck, h->ck,
+    k_pi_grad<<<(unsigned)blocks, 128, 0, ls>>>(h->m, h->c, j0, j1, checkpoint_every, n_ck, h->ck,
                                                 h->n_sims, h->phi, h->cnt, h->dphi);
-    MC_CUDA(h, cudaGetLastError());
   }
-  k_grad_mean<<<1, kGradThreads, 0, st>>>(h->phi, h->dphi, j0, j1, h->gmean);
+  k_grad_mean<<<1, kGradThreads, 0, ls>>>(h->phi, h->dphi, j0, j1, h->gmean);
+  const mc_status s = launch_stats(h, j0, j1, ls);
+  join_stream(h, st, ls);
   MC_CUDA(h, cudaGetLastError());
-  const mc_status s = launch_stats(h, j0, j1, st);
   if (s != MC_OK) return s;
   MC_CUDA(h, cudaEventRecord(h->ev1, st));
   h->ran = true;

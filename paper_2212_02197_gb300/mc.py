@@ -113,6 +113,8 @@ def lib():
                                             C.POINTER(McStats)]
             L.mc_set_graph.argtypes = [H, C.c_int]
             L.mc_autotune.argtypes = [H, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
+            L.mc_set_sm_partition.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
+            L.mc_set_sm_partition.restype = C.c_int
             L.mc_exp_batch.argtypes = [_dp, C.c_int64, _dp]
             L.mc_exp_batch.restype = C.c_int
             L.mc_set_pi_gains.argtypes = [H, C.c_double, C.c_double, C.c_double]
@@ -221,6 +223,13 @@ class MonteCarlo:
     def set_graph(self, on: bool = True):
         """Replay each range's launches from a captured CUDA graph."""
         _check(lib().mc_set_graph(self._h, 1 if on else 0), self._h)
+
+    def set_sm_partition(self, n_sms: int) -> int:
+        """Run on a partition of at least n_sms SMs (0: the whole GPU); returns
+        the SM count actually used."""
+        got = C.c_int32()
+        _check(lib().mc_set_sm_partition(self._h, int(n_sms), C.byref(got)), self._h)
+        return got.value
 
     def autotune(self, probe_steps: int = 8, stream=None) -> int:
         """Resident threads per SM of the persistent schedule, chosen by timing."""

@@ -392,3 +392,44 @@ def test_graph_replay_and_autotune_keep_results():
     h.sync()
     assert np.array_equal(h.phi()[10:50], phi0[10:50])
     h.close()
+
+
+def torch_sms():
+    import torch
+
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def test_sm_partition_keeps_results():
+    """A green-context partition of 16 SMs changes where trajectories run,
+    not what they compute: Phi and the counters equal the whole-GPU run, for
+    the persistent and the static schedule and for the PI gradient."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=20)
+    for sched in ("persistent", "static"):
+        c = dict(w["nmpc"], schedule=sched)
+        h = mc.MonteCarlo(m, c, 300, w["seed"])
+        h.run()
+        h.sync()
+        phi0, cnt0 = h.phi(), h.counters()
+        sms = torch_sms()
+        got = h.set_sm_partition(16)
+        assert 16 <= got < sms
+        h.run()
+        st = h.stats()
+        assert np.array_equal(h.phi(), phi0)
+        cnt = h.counters()
+        for k in cnt0:
+            assert np.array_equal(cnt[k], cnt0[k])
+        assert st["n_traj"] == 300 and st["gpu_ms"] > 0
+        assert h.set_sm_partition(0) == sms
+        h.close()
+    hp = mc.MonteCarlo(m, w["pi"], 200, w["seed"])
+    hp.pi_grad(20)
+    g0 = hp.grad()
+    hp.set_sm_partition(8)
+    hp.pi_grad(20)
+    assert np.array_equal(hp.grad(), g0)
+    with pytest.raises(mc.McError):
+        hp.set_sm_partition(-1)
+    hp.close()
