@@ -49,7 +49,7 @@ class Model(C.Structure):
                 ("beta", C.c_double), ("cA_in", C.c_double), ("cB_in", C.c_double),
                 ("T_in", C.c_double), ("sigma", C.c_double * 3), ("meas_sd", C.c_double),
                 ("Ts", C.c_double), ("t0", C.c_double), ("n_steps", C.c_int32),
-                ("n_em", C.c_int32), ("n_sp", C.c_int32), ("pad0", C.c_int32),
+                ("n_em", C.c_int32), ("n_sp", C.c_int32), ("Ea_plant_only", C.c_int32),
                 ("sp_time", C.c_double * MAX_SP), ("sp_value", C.c_double * MAX_SP),
                 ("Ea_logsd", C.c_double), ("dTin_step", C.c_double)]
 
@@ -148,6 +148,7 @@ def make_model(md: dict) -> Model:
         m.sigma[i] = float(md["sigma"][i])
     m.n_steps = int(md["n_steps"])
     m.n_em = int(md["n_em"])
+    m.Ea_plant_only = 1 if md.get("Ea_plant_only", False) else 0
     sp_t, sp_v = md["sp_time"], md["sp_value"]
     assert len(sp_t) == len(sp_v) and 1 <= len(sp_t) <= MAX_SP
     m.n_sp = len(sp_t)

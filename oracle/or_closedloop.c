@@ -40,6 +40,9 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
              or_traj_out* out, double* trace) {
   double EaR, t_d, dTin;
   or_traj_params(m, seed, j, &EaR, &t_d, &dTin);
+  /* the controller's model (EKF, OCP, steady-state input): the trajectory's
+   * E_a/R, or the nominal one when the perturbation is the plant's alone */
+  const double EaR_c = m->Ea_plant_only ? m->EaR : EaR;
   /* this trajectory's horizon and SQP iteration limit (uneven batches) */
   or_ctrl cj = *c_in;
   or_traj_horizon(c_in, seed, j, &cj.N, &cj.sqp_max_it);
@@ -64,7 +67,7 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
   if (c->kind == 0) {
     /* first OCP guess: steady-state input of the first set-point (clipped),
      * states at the initial estimate, multipliers zero */
-    double v0 = or_Fss(m, EaR, or_zbar(m, m->t0)) / Fconv;
+    double v0 = or_Fss(m, EaR_c, or_zbar(m, m->t0)) / Fconv;
     v0 = fmin(fmax(v0, c->u_min / c->u_scale), c->u_max / c->u_scale);
     x[0] = xhat / c->x_scale;
     for (int k = 0; k < N; ++k) {
@@ -94,12 +97,12 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
     double its = 0.0;
     if (c->kind == 0) {
       /* CD-EKF: prediction from t_{i-1} (none before the first sample), filtering */
-      if (i > 0) or_ekf_predict(m, EaR, c->n_rk4, F_prev, &xhat, &P);
+      if (i > 0) or_ekf_predict(m, EaR_c, c->n_rk4, F_prev, &xhat, &P);
       or_ekf_filter(m, y, &xhat, &P, NULL);
       /* regulator: OCP over the horizon t_{i+1} .. t_{i+N} */
       for (int k = 1; k <= N; ++k) zb[k] = or_zbar(m, m->t0 + (double)(i + k) * m->Ts);
       or_sqp_info info;
-      or_sqp(m, c, EaR, xhat / c->x_scale, zb, u, x, lam, pil, piu, &info);
+      or_sqp(m, c, EaR_c, xhat / c->x_scale, zb, u, x, lam, pil, piu, &info);
       out->n_ocp++;
       out->sqp_iters += info.iters;
       out->ls_trials += info.ls_trials;
@@ -119,7 +122,7 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
         piu[k] = piu[k + 1];
       }
     } else {
-      const double ubar = or_Fss(m, EaR, zbar_i);
+      const double ubar = or_Fss(m, EaR_c, zbar_i);
       F = or_pi_step(c, m->Ts, zbar_i, y, ubar, &Ihat);
     }
     trace_row(trace, i, cT, y, (c->kind == 0) ? xhat / m->V : NAN, F * 60000.0, its);

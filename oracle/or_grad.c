@@ -67,7 +67,7 @@ double or_pi_phi_cs(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t 
     if (i == K) break;
     const cplx y = cT + m->meas_sd * or_meas_noise(seed, j, i);
     const double zbar_i = or_zbar(m, t_i);
-    const double ubar = or_Fss(m, EaR, zbar_i);
+    const double ubar = or_Fss(m, m->Ea_plant_only ? m->EaR : EaR, zbar_i);
     /* Eq. (PI) */
     const cplx e = zbar_i - y;
     const cplx P = kP * e;

@@ -48,7 +48,8 @@ typedef struct {
   int32_t n_steps;      /* control steps K; Phi has K+1 terms                */
   int32_t n_em;         /* Euler-Maruyama substeps per sample, N_s           */
   int32_t n_sp;         /* number of set-point segments                      */
-  int32_t pad0;
+  int32_t Ea_plant_only; /* 1: the E_a/R perturbation acts on the plant only;
+                            the controller's model keeps the nominal E_a/R  */
   double sp_time[OR_MAX_SP];   /* segment s starts at sp_time[s]             */
   double sp_value[OR_MAX_SP];  /* set-point temperature of segment s (K)     */
   double Ea_logsd;      /* per-trajectory lognormal sd of E_a/R, 0 = off    */

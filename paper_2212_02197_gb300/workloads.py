@@ -48,8 +48,9 @@ SCHEDULE_PAPER = ((0.0, 276.0), (20.0, 282.0), (40.0, 290.0), (80.0, 340.0),
 
 
 def model(n_steps: int, Ts: float = 0.5, n_em: int = 10, Ea_logsd: float = 0.0,
-          dTin_step: float = 0.0, schedule=SCHEDULE) -> dict:
-    """Plant/model/closed-loop dict."""
+          dTin_step: float = 0.0, schedule=SCHEDULE, Ea_plant_only: bool = False) -> dict:
+    """Plant/model/closed-loop dict.  Ea_plant_only: the E_a/R perturbation acts
+    on the plant alone (the controller's model keeps the nominal value)."""
     m = dict(CSTR)
     m["sigma"] = [1e-2 * m["cA_in"], 1e-2 * m["cB_in"], 1e-2 * m["T_in"]]
     m["meas_sd"] = 0.1
@@ -61,6 +62,7 @@ def model(n_steps: int, Ts: float = 0.5, n_em: int = 10, Ea_logsd: float = 0.0,
     m["sp_value"] = [float(v) for _, v in schedule]
     m["Ea_logsd"] = float(Ea_logsd)
     m["dTin_step"] = float(dTin_step)
+    m["Ea_plant_only"] = bool(Ea_plant_only)
     return m
 
 
@@ -103,6 +105,12 @@ WORKLOADS = {
     "cstr_100k_x240_N30_mixed": dict(model=model(240, Ea_logsd=0.02),
                                      nmpc=nmpc(30, precision="mixed"), pi=None,
                                      n_traj=100000, seed=SEED),
+    # model mismatch: the paper-scale FP64 study with E_a/R lognormal sd 2 % in the
+    # plant only; the controllers' models (EKF, OCP, steady-state input) keep the
+    # nominal E_a/R
+    "cstr_30k_x240_N20_fp64_mismatch": dict(
+        model=model(240, dTin_step=5.0, Ea_logsd=0.02, Ea_plant_only=True), nmpc=nmpc(20),
+        pi=pi(), n_traj=30000, seed=SEED),
     # uneven batches: 262,144 trajectories, 120 steps, horizon uniform on 10..40 and
     # SQP iteration limit uniform on 5..30 per trajectory, persistent schedule
     "cstr_262k_x120_N10to40_uneven": dict(

@@ -135,3 +135,38 @@ def test_uneven_trajectory_uses_its_horizon():
     c = dict(w["nmpc"], sqp_max_it=5, sqp_max_it_min=5)
     r = oracle.run(m, c, w["seed"], 0, 6)
     assert np.all(r["sqp_iters"] <= 5 * 20)
+
+
+# ------------------------------------------------------------------ model mismatch
+
+def test_mismatch_first_input_is_the_nominal_controllers():
+    """With the E_a/R perturbation in the plant only, the controller sees at
+    sample 0 only the initial state and the measurement, so its first input is
+    the one of the unperturbed study, bit for bit; when the controller knows
+    the trajectory's E_a/R (the default) the first input moves with it."""
+    w = W.get("cstr_30k_x240_N20_fp64_mismatch")
+    m_mis = dict(w["model"], n_steps=3)
+    m_nom = dict(m_mis, Ea_logsd=0.0)
+    m_known = dict(m_mis, Ea_plant_only=False)
+    # the first sample's (applied input, SQP iterations of its OCP); the NMPC's
+    # first inputs sit on the lower bound, its iteration counts still differ
+    for kind in ("nmpc", "pi"):
+        moved_known, moved_later = [], []
+        for j in (0, 1, 2):
+            t_mis = oracle.traj(m_mis, w[kind], w["seed"], j, with_trace=True)["trace"]
+            t_nom = oracle.traj(m_nom, w[kind], w["seed"], j, with_trace=True)["trace"]
+            t_kn = oracle.traj(m_known, w[kind], w["seed"], j, with_trace=True)["trace"]
+            assert np.array_equal(t_mis[0, 3:5], t_nom[0, 3:5]), (kind, j)
+            moved_known.append(not np.array_equal(t_kn[0, 3:5], t_nom[0, 3:5]))
+            # from sample 1 on, the perturbed plant has moved the measurement
+            moved_later.append(t_mis[1, 1] != t_nom[1, 1])
+        assert all(moved_known) and all(moved_later), (kind, moved_known, moved_later)
+
+
+def test_mismatch_flag_is_inert_without_perturbation():
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=20)
+    for kind in ("nmpc", "pi"):
+        a = oracle.run(m, w[kind], w["seed"], 0, 6)["phi"]
+        b = oracle.run(dict(m, Ea_plant_only=True), w[kind], w["seed"], 0, 6)["phi"]
+        assert np.array_equal(a, b)
