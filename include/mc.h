@@ -63,7 +63,11 @@ typedef enum { MC_CTRL_NMPC = 0, MC_CTRL_PI = 1 } mc_ctrl_kind;
 typedef enum { MC_FP64 = 0, MC_MIXED = 1 } mc_precision;
 typedef enum {
   MC_QP_ACTIVE_SET = 0,   /* Riccati-based primal active-set method          */
-  MC_QP_IPM = 1           /* Riccati-based primal-dual interior point (Mehrotra) */
+  MC_QP_IPM = 1,          /* Riccati-based primal-dual interior point (Mehrotra) */
+  MC_QP_ACTIVE_SET_WARP = 2  /* the active-set method with a parallel-in-horizon
+                                Riccati recursion, one warp per QP (the lanes
+                                over the stages); mc_qp_solve_batch only --
+                                the closed loop runs one trajectory per lane */
 } mc_qp_solver;
 
 /* Plant, NMPC model and closed-loop set-up (Sec. VI, VII-A). */
@@ -75,7 +79,11 @@ typedef struct {
   int32_t n_steps;        /* control steps K (Phi has K+1 terms)               */
   int32_t n_em;           /* Euler-Maruyama substeps per sample, N_s           */
   int32_t n_setpoints;    /* 1..MC_MAX_SETPOINTS                               */
-  int32_t reserved0;
+  int32_t Ea_plant_only;  /* 0: the E_a/R perturbation is known to the
+                             controller (its EKF and OCP model use the
+                             trajectory's E_a/R); 1: model mismatch, the
+                             perturbation acts on the plant only and the
+                             controller keeps the nominal E_a/R              */
   const double* sp_time;  /* host, n_setpoints: segment start times, ascending */
   const double* sp_value; /* host, n_setpoints: set-point temperatures (K)     */
   double Ea_logsd;        /* lognormal sd of E_a/R per trajectory, 0 = off     */

@@ -22,6 +22,7 @@
 #include "../../include/mc.h"
 #include "mc_closedloop.cuh"
 #include "mc_grad.cuh"
+#include "mc_qp_par.cuh"
 
 namespace mc {
 
@@ -281,6 +282,46 @@ __global__ void k_qp_batch(int N, int64_t n, int solver, int max_it, double tol,
   d.status[t] = r.status;
 }
 
+// One warp per QP: the parallel-in-horizon solver (lanes over the stages).
+constexpr int kQpWarpsPerBlock = 4;
+__global__ void __launch_bounds__(32 * kQpWarpsPerBlock)
+    k_qp_batch_warp(int N, int64_t n, int max_it, QpBatch d, double* ws, int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * kQpWarpsPerBlock + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;  // whole warps leave together
+  const Ws w{ws + t, ld, N + 1};
+  const int64_t o1 = t * N, o2 = t * (N + 1);
+  for (int k = lane; k < N; k += 32) {
+    w(EA, k) = d.A[o1 + k];
+    w(EB, k) = d.B[o1 + k];
+    w(EG, k) = d.b[o1 + k];
+    w(QR, k) = d.r[o1 + k];
+    w(LB, k) = d.lb[o1 + k];
+    w(UB, k) = d.ub[o1 + k];
+  }
+  for (int k = lane; k <= N; k += 32) {
+    w(WXX, k) = d.Wxx[o2 + k];
+    w(WXU, k) = d.Wxu[o2 + k];
+    w(WUU, k) = d.Wuu[o2 + k];
+    w(EQ, k) = d.q[o2 + k];
+  }
+  __syncwarp();
+  const QpResult r = qp_active_set_warp(w, N, true, max_it, lane);
+  __syncwarp();
+  for (int k = lane; k < N; k += 32) {
+    d.du[o1 + k] = w(DU, k);
+    d.mu[o1 + k] = w(MU, k);
+    d.nul[o1 + k] = w(NUL, k);
+    d.nuu[o1 + k] = w(NUU, k);
+    d.dx[o2 + k + 1] = w(DX, k + 1);
+  }
+  if (lane == 0) {
+    d.dx[o2] = 0.0;
+    d.iters[t] = r.iters;
+    d.status[t] = r.status;
+  }
+}
+
 struct OcpBatch {
   const double *x0, *EaR, *zbar;
   double *u, *x, *lam, *pil, *piu, *kkt;
@@ -432,6 +473,9 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
     if (!(cc->sqp_tol > 0)) return bad("sqp_tol must be > 0");
     if (!(mm->meas_sd > 0)) return bad("the CD-EKF needs a measurement noise sd > 0");
     if (!(cc->u_scale > 0) || !(cc->x_scale > 0)) return bad("u_scale and x_scale must be > 0");
+    if (cc->qp_solver == MC_QP_ACTIVE_SET_WARP)
+      return bad("the warp-per-QP solver is a building block (mc_qp_solve_batch); the closed "
+                 "loop runs one trajectory per lane");
     if (cc->qp_solver != MC_QP_ACTIVE_SET && cc->qp_solver != MC_QP_IPM)
       return bad("unknown QP solver");
     if (cc->qp_solver == MC_QP_IPM && (cc->ip_max_it < 1 || !(cc->ip_tol > 0)))
@@ -456,7 +500,9 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
     if (s > 0 && !(mm->sp_time[s] > mm->sp_time[s - 1]))
       return bad("set-point times must increase");
   }
+  if (mm->Ea_plant_only != 0 && mm->Ea_plant_only != 1) return bad("Ea_plant_only must be 0 or 1");
   m->Ea_logsd = mm->Ea_logsd; m->dTin = mm->dT_in_step;
+  m->Ea_plant_only = mm->Ea_plant_only;
   m->iV = 1.0 / mm->V; m->ib = 1.0 / mm->beta;
   m->key0 = (uint32_t)seed; m->key1 = (uint32_t)(seed >> 32);
   memset(c, 0, sizeof(*c));
@@ -1145,6 +1191,8 @@ mc_status mc_qp_solve_batch(int32_t N, int64_t n, int32_t solver, int32_t max_it
                             double* nuu, int32_t* iters, int32_t* status) {
   if (N < 1 || N > MC_MAX_HORIZON || n < 0 || max_it < 1)
     return fail(nullptr, MC_EINVAL, "mc_qp_solve_batch: bad sizes");
+  if (solver != MC_QP_ACTIVE_SET && solver != MC_QP_IPM && solver != MC_QP_ACTIVE_SET_WARP)
+    return fail(nullptr, MC_EINVAL, "mc_qp_solve_batch: unknown solver");
   if (n == 0) return MC_OK;
   const size_t n1 = (size_t)n * N, n2 = (size_t)n * (N + 1);
   QpBatch d{};
@@ -1180,7 +1228,11 @@ mc_status mc_qp_solve_batch(int32_t N, int64_t n, int32_t solver, int32_t max_it
   if (!ok) {
     s = fail(nullptr, MC_ENOMEM, "mc_qp_solve_batch: allocation");
   } else {
-    k_qp_batch<<<(unsigned)((n + 127) / 128), 128>>>(N, n, solver, max_it, tol, d, ws, ld);
+    if (solver == MC_QP_ACTIVE_SET_WARP)
+      k_qp_batch_warp<<<(unsigned)((n + kQpWarpsPerBlock - 1) / kQpWarpsPerBlock),
+                        32 * kQpWarpsPerBlock>>>(N, n, max_it, d, ws, ld);
+    else
+      k_qp_batch<<<(unsigned)((n + 127) / 128), 128>>>(N, n, solver, max_it, tol, d, ws, ld);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(du, d.du, sizeof(double) * n1, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(mu, d.mu, sizeof(double) * n1, cudaMemcpyDeviceToHost);

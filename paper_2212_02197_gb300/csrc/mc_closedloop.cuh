@@ -67,7 +67,7 @@ __device__ TrajOut traj_pi(const DevModel& m, const DevCtrl& c, uint32_t j) {
     phi += ez * ez;
     if (i == K) break;
     const double y = cT + m.meas_sd * (double)meas_noise<R>(m, j, (uint32_t)i);
-    const double ubar = Fss(m, tp.EaR, zi);
+    const double ubar = Fss(m, tp.EaR_c, zi);
     const double F = (double)pi_step<R>(c, (R)m.Ts, (R)zi, (R)y, (R)ubar, Ihat);
     plant_interval<R>(m, tp, j, i, F, n);
   }
@@ -101,7 +101,7 @@ __device__ __forceinline__ void nmpc_begin(const DevModel& m, const DevCtrl& c, 
   T.F_prev = 0.0;
   T.phi = 0.0;
   T.out = TrajOut{};
-  double v0 = Fss(m, T.tp.EaR, zbar(m, m.t0)) / c.Fconv;
+  double v0 = Fss(m, T.tp.EaR_c, zbar(m, m.t0)) / c.Fconv;
   v0 = fmin(fmax(v0, c.vmin), c.vmax);
   const double ixs = 1.0 / c.x_scale;
   for (int k = 0; k < T.tp.N; ++k) {
@@ -136,13 +136,13 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
   const double y = cT + m.meas_sd * (double)meas_noise<R>(m, T.j, (uint32_t)T.i);
   if (T.i > 0) {
     R xr = (R)T.xhat, Pr = (R)T.P;
-    ekf_predict<R>(m, (R)T.tp.EaR, c.n_rk4, (R)T.F_prev, xr, Pr);
+    ekf_predict<R>(m, (R)T.tp.EaR_c, c.n_rk4, (R)T.F_prev, xr, Pr);
     T.xhat = (double)xr;
     T.P = (double)Pr;
   }
   ekf_filter(m, y, T.xhat, T.P);
   for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(T.i + k) * m.Ts);
-  sqp_start<R>(m, c, T.tp.EaR, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s);
+  sqp_start<R>(m, c, T.tp.EaR_c, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s);
   return true;
 }
 
@@ -212,7 +212,7 @@ __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, co
     while (!sqp_check<R>(c, w, s)) {
       int r;
       do {
-        sqp_eval_trial<R>(m, c, T.tp.EaR, w, s);
+        sqp_eval_trial<R>(m, c, T.tp.EaR_c, w, s);
         r = sqp_trial_result<R>(c, w, s);
       } while (r == 2);
       if (r == 1) break;
@@ -288,14 +288,14 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       for (unsigned rem = tm; rem; rem &= rem - 1u) {
         const int o = __ffs(rem) - 1;
         const int No = __shfl_sync(0xffffffffu, s.N, o);
-        const double EaRo = __shfl_sync(0xffffffffu, T.tp.EaR, o);
+        const double EaRo = __shfl_sync(0xffffffffu, T.tp.EaR_c, o);
         const Ws wo{w.p + (o - lane), w.ld, w.N1};
         sqp_shoot_trial_coop<R>(m, c, EaRo, No, wo, lane);
       }
       __syncwarp();  // the helpers' A_k, B_k, g_k are visible to the owners
-      if (phase == kTrial) sqp_eval_trial_shot<R>(m, c, T.tp.EaR, w, s);
+      if (phase == kTrial) sqp_eval_trial_shot<R>(m, c, T.tp.EaR_c, w, s);
     } else if (phase == kTrial) {
-      sqp_eval_trial<R>(m, c, T.tp.EaR, w, s);
+      sqp_eval_trial<R>(m, c, T.tp.EaR_c, w, s);
     }
     if (phase == kTrial) {
       const int r = sqp_trial_result<R>(c, w, s);

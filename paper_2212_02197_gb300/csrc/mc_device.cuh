@@ -26,7 +26,8 @@ struct DevModel {
   double sigma[3];
   double meas_sd;
   double Ts, t0;
-  int n_steps, n_em, n_sp, pad0;
+  int n_steps, n_em, n_sp;
+  int Ea_plant_only;   // 1: the controller's model keeps the nominal E_a/R
   double sp_time[kMaxSp], sp_value[kMaxSp];
   double Ea_logsd, dTin;
   double iV, ib;       // 1/V and 1/beta
@@ -120,7 +121,9 @@ __device__ __forceinline__ R meas_noise(const DevModel& m, uint32_t j, uint32_t 
 }
 
 struct TrajParams {
-  double EaR, t_d, dTin;
+  double EaR;      // the plant's E_a/R
+  double EaR_c;    // the controller's (EKF, OCP model, steady-state input)
+  double t_d, dTin;
   int N, max_it;   // horizon and SQP iteration limit of this trajectory's OCPs
 };
 
@@ -148,6 +151,7 @@ __device__ __forceinline__ TrajParams traj_params(const DevModel& m, const DevCt
   p.dTin = (w.z & 1u) ? m.dTin : -m.dTin;
   const double2 z = Normal2<double>::from(philox4x32_10(make_uint4(1u, j, 3u, 0u), m.key0, m.key1));
   p.EaR = (m.Ea_logsd != 0.0) ? m.EaR * exp(m.Ea_logsd * z.x) : m.EaR;
+  p.EaR_c = m.Ea_plant_only ? m.EaR : p.EaR;
   return p;
 }
 

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
       CK(3, i / C) = Ihat;
     }
     const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
-    const double ubar = Fss(m, tp.EaR, zi);
+    const double ubar = Fss(m, tp.EaR_c, zi);
     const double F = pi_step<double>(c, m.Ts, zi, y, ubar, Ihat);
     plant_interval<double>(m, tp, j, i, F, n);
   }
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
       const double cT = nn[2] / m.V;
       const double zi = zbar(m, m.t0 + (double)i * m.Ts);
       const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
-      const double F = pi_step<double>(c, m.Ts, zi, y, Fss(m, tp.EaR, zi), Ih);
+      const double F = pi_step<double>(c, m.Ts, zi, y, Fss(m, tp.EaR_c, zi), Ih);
       plant_interval<double>(m, tp, j, i, F, nn);
     }
     for (int i = i1 - 1; i >= i0; --i) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
       const double zi = zbar(m, m.t0 + (double)i * m.Ts);
       const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
       double e, uhat;
-      const double F = pi_step<double>(c, m.Ts, zi, y, Fss(m, tp.EaR, zi), Ih2, &e, &uhat);
+      const double F = pi_step<double>(c, m.Ts, zi, y, Fss(m, tp.EaR_c, zi), Ih2, &e, &uhat);
       // substep states and noise of this sample
       for (int s = 0; s < m.n_em; ++s) {
         const int64_t ks = (int64_t)i * m.n_em + s;

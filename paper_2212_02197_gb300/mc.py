@@ -25,7 +25,7 @@ COUNTER_NAMES = ["n_ocp_failed", "sqp_iters", "ls_trials", "n_hess_reset", "n_ls
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_ENOTRUN = 0, 1, 2, 3, 4, 5
 MC_WARN_NONFINITE = 100
-QP_SOLVERS = {"active_set": 0, "ipm": 1}
+QP_SOLVERS = {"active_set": 0, "ipm": 1, "active_set_warp": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 KINDS = {"nmpc": 0, "pi": 1}
 SCHEDULES = {"static": 0, "persistent": 1}
@@ -39,7 +39,7 @@ class McModel(C.Structure):
                 ("beta", C.c_double), ("cA_in", C.c_double), ("cB_in", C.c_double),
                 ("T_in", C.c_double), ("sigma", C.c_double * 3), ("meas_sd", C.c_double),
                 ("Ts", C.c_double), ("t0", C.c_double), ("n_steps", C.c_int32),
-                ("n_em", C.c_int32), ("n_setpoints", C.c_int32), ("reserved0", C.c_int32),
+                ("n_em", C.c_int32), ("n_setpoints", C.c_int32), ("Ea_plant_only", C.c_int32),
                 ("sp_time", _dp), ("sp_value", _dp), ("Ea_logsd", C.c_double),
                 ("dT_in_step", C.c_double)]
 
@@ -157,6 +157,7 @@ def make_model(md: dict):
         m.sigma[i] = float(md["sigma"][i])
     m.n_steps, m.n_em = int(md["n_steps"]), int(md["n_em"])
     m.n_setpoints = len(sp_t)
+    m.Ea_plant_only = 1 if md.get("Ea_plant_only", False) else 0
     m.sp_time, m.sp_value = _p(sp_t), _p(sp_v)
     return m, (sp_t, sp_v)
 
@@ -344,7 +345,7 @@ def qp_solve_batch(A, B, b, Wxx, Wxu, Wuu, q, r, lb, ub, solver="active_set", ma
                                                                  lb, ub)]
     n, N = arrs[1].shape
     if max_it is None:
-        max_it = 10 * N + 20 if solver == "active_set" else 60
+        max_it = 10 * N + 20 if solver in ("active_set", "active_set_warp") else 60
     du, mu, nul, nuu = (np.empty((n, N)) for _ in range(4))
     dx = np.empty((n, N + 1))
     it = np.empty(n, dtype=np.int32)

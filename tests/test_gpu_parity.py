@@ -97,21 +97,43 @@ def test_device_exp_within_two_ulp():
     assert y[-2] == np.inf and y[-1] == 0.0
 
 
-@pytest.mark.parametrize("N", [1, 2, 5, 20, 40, 64])
-@pytest.mark.parametrize("solver", ["active_set", "ipm"])
+@pytest.mark.parametrize("N", [1, 2, 5, 20, 31, 32, 33, 40, 60, 64])
+@pytest.mark.parametrize("solver", ["active_set", "ipm", "active_set_warp"])
 def test_qp_matches_oracle(N, solver):
     rng = np.random.default_rng(N)
     n = 300
     qp = random_qps(n, N, rng)
     dev = mc.qp_solve_batch(*qp, solver=solver)
     assert np.all(dev["status"] == 0), np.flatnonzero(dev["status"])
-    tol = dict(active_set=(1e-9, 1e-10), ipm=(1e-6, 1e-6))[solver]
+    tol = dict(active_set=(1e-9, 1e-10), ipm=(1e-6, 1e-6), active_set_warp=(1e-9, 1e-10))[solver]
     for i in range(n):
         ref = oracle.qp_solve(*[a[i] for a in qp])
         assert ref["status"] == 0
         for key in ("du", "dx", "mu", "nul", "nuu"):
             scale = 1.0 + np.max(np.abs(ref[key]))
             assert np.allclose(dev[key][i], ref[key], rtol=tol[0], atol=tol[1] * scale), (i, key)
+
+
+@pytest.mark.parametrize("N", [3, 20, 60, 64])
+def test_warp_qp_follows_the_serial_active_set(N):
+    """The parallel-in-horizon solver takes the same working-set steps as the
+    serial active-set method (same iteration counts) and lands on the same
+    point to rounding; bounds that start active and a horizon that fills two
+    stages per lane are covered."""
+    rng = np.random.default_rng(100 + N)
+    n = 500
+    qp = random_qps(n, N, rng)
+    a = mc.qp_solve_batch(*qp, solver="active_set")
+    b = mc.qp_solve_batch(*qp, solver="active_set_warp")
+    assert np.array_equal(a["status"], b["status"])
+    assert np.array_equal(a["iters"], b["iters"])
+    for key in ("du", "dx", "mu", "nul", "nuu"):
+        scale = 1.0 + np.max(np.abs(a[key]), axis=1, keepdims=True)
+        assert np.all(np.abs(a[key] - b[key]) <= 1e-10 * scale), key
+    # active bounds are hit exactly
+    lb, ub = qp[8], qp[9]
+    on = (np.abs(b["du"] - lb) == 0) | (np.abs(b["du"] - ub) == 0)
+    assert on.any()
 
 
 # ------------------------------------------------------------------ OCPs
@@ -310,6 +332,28 @@ def test_ipm_closed_loop_matches_oracle():
     ref = oracle.run(m, c, w["seed"], 0, 16)
     compare_phi(h.phi(), ref, h.counters(), 1e-6)
     h.close()
+
+
+@pytest.mark.parametrize("kind", ["nmpc", "pi"])
+def test_model_mismatch_matches_oracle(kind):
+    """E_a/R perturbed in the plant only (the controllers keep the nominal
+    model): 100 trajectories of the paper-scale mismatch study, 80 steps,
+    against the oracle; the variant differs from the matched one."""
+    w = W.get("cstr_30k_x240_N20_fp64_mismatch")
+    m = dict(w["model"], n_steps=80)
+    n = 100
+    h = mc.MonteCarlo(m, w[kind], n, w["seed"])
+    h.run()
+    h.sync()
+    phi, cnt = h.phi(), h.counters()
+    h.close()
+    ref = oracle.run(m, w[kind], w["seed"], 0, n)
+    compare_phi(phi, ref, cnt, 1e-6 if kind == "nmpc" else 1e-12)
+    hk = mc.MonteCarlo(dict(m, Ea_plant_only=False), w[kind], n, w["seed"])
+    hk.run()
+    hk.sync()
+    assert not np.array_equal(hk.phi(), phi)
+    hk.close()
 
 
 # ------------------------------------------------------------------ schedules
