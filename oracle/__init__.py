@@ -20,7 +20,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRC = ["or_random.c", "or_model.c", "or_sqp.c", "or_closedloop.c", "or_grad.c"]
+_SRC = ["or_random.c", "or_model.c", "or_sqp.c", "or_closedloop.c", "or_grad.c",
+        "or_nmpc3.c"]
 MAX_SP = 16
 MAX_N = 64
 
@@ -56,7 +57,7 @@ class Model(C.Structure):
 
 class Ctrl(C.Structure):
     _fields_ = [("kind", C.c_int32), ("N", C.c_int32), ("n_rk4", C.c_int32),
-                ("sqp_max_it", C.c_int32), ("ls_max", C.c_int32), ("pad0", C.c_int32),
+                ("sqp_max_it", C.c_int32), ("ls_max", C.c_int32), ("nx_model", C.c_int32),
                 ("u_min", C.c_double), ("u_max", C.c_double), ("kP", C.c_double),
                 ("kI", C.c_double), ("kaw", C.c_double), ("Qz", C.c_double),
                 ("P0", C.c_double), ("sqp_tol", C.c_double), ("u_scale", C.c_double),
@@ -126,6 +127,19 @@ def lib():
                                   C.POINTER(TrajOut), _dp]
             L.or_run.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64, C.c_int64,
                                  C.c_int64, C.c_int, C.POINTER(TrajOut)]
+            L.or_drift3.argtypes = [C.POINTER(Model), C.c_double, C.c_double, _dp, C.c_double,
+                                    _dp, _dp, _dp]
+            L.or_rk4_interval3.argtypes = [C.POINTER(Model), C.c_double, C.c_int, C.c_double,
+                                           _dp, C.c_double, C.c_double, _dp, _dp, _dp]
+            L.or_ekf3_predict.argtypes = [C.POINTER(Model), C.c_double, C.c_int, C.c_double,
+                                          _dp, _dp]
+            L.or_ekf3_filter.argtypes = [C.POINTER(Model), C.c_double, _dp, _dp, _dp]
+            L.or_qp3_solve.argtypes = [C.c_int] + [_dp] * 15 + [C.POINTER(C.c_int)]
+            L.or_qp3_solve.restype = C.c_int
+            L.or_bfgs_blockn.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.or_sqp3.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_double, _dp, _dp, _dp,
+                                  _dp, _dp, _dp, _dp, C.POINTER(SqpInfo)]
+            L.or_sqp3.restype = C.c_int
             L.or_pi_phi_cs.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64,
                                        C.c_int64, C.c_int, C.c_double, _dp]
             L.or_pi_phi_cs.restype = C.c_double
@@ -166,6 +180,7 @@ def make_ctrl(cd: dict) -> Ctrl:
     for k in ("u_min", "u_max", "kP", "kI", "kaw", "Qz", "P0", "sqp_tol", "u_scale",
               "x_scale"):
         setattr(c, k, float(cd[k]))
+    c.nx_model = int(cd.get("nx_model", 1))
     c.N_min = int(cd.get("N_min", 0))
     c.it_min = int(cd.get("sqp_max_it_min", 0))
     assert 1 <= c.N <= MAX_N
@@ -369,3 +384,92 @@ def traj_horizon(ctrl: dict, seed, j):
     N, it = C.c_int(), C.c_int()
     L.or_traj_horizon(C.byref(c), seed, j, C.byref(N), C.byref(it))
     return N.value, it.value
+
+
+# ---------------------------------------------------------------- three-state NMPC model
+
+def _arr(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if n is None else a.reshape(n)
+
+
+def drift3(model: dict, n, F, EaR=None, T_in=None):
+    L = lib()
+    m = make_model(model)
+    n = _arr(n).copy()
+    f, J, fF = np.zeros(3), np.zeros(9), np.zeros(3)
+    L.or_drift3(C.byref(m), model["EaR"] if EaR is None else EaR,
+                model["T_in"] if T_in is None else T_in, _p(n), F, _p(f), _p(J), _p(fF))
+    return f, J.reshape(3, 3), fF
+
+
+def rk4_interval3(model: dict, n_rk4, Ts, x0, v, Fconv, EaR=None):
+    L = lib()
+    m = make_model(model)
+    x0 = _arr(x0).copy()
+    xF, A, B = np.zeros(3), np.zeros(9), np.zeros(3)
+    L.or_rk4_interval3(C.byref(m), model["EaR"] if EaR is None else EaR, n_rk4, Ts, _p(x0), v,
+                       Fconv, _p(xF), _p(A), _p(B))
+    return xF, A.reshape(3, 3), B
+
+
+def ekf3_predict(model: dict, n_rk4, F, x, P, EaR=None):
+    L = lib()
+    m = make_model(model)
+    x = _arr(x).copy()
+    P = _arr(P).reshape(9).copy()
+    L.or_ekf3_predict(C.byref(m), model["EaR"] if EaR is None else EaR, n_rk4, F, _p(x), _p(P))
+    return x, P.reshape(3, 3)
+
+
+def ekf3_filter(model: dict, y, x, P):
+    L = lib()
+    m = make_model(model)
+    x = _arr(x).copy()
+    P = _arr(P).reshape(9).copy()
+    Ps = np.zeros(9)
+    L.or_ekf3_filter(C.byref(m), y, _p(x), _p(P), _p(Ps))
+    return x, P.reshape(3, 3), Ps.reshape(3, 3)
+
+
+def qp3_solve(A, B, b, Wxx, Wxu, Wuu, q, r, lb, ub):
+    """Three-state QP: A (N,3,3), B, b (N,3), Wxx (N+1,3,3), Wxu (N+1,3), Wuu (N+1),
+    q (N+1,3), r, lb, ub (N)."""
+    L = lib()
+    N = len(r)
+    ins = [_arr(a).copy() for a in (A, B, b, Wxx, Wxu, Wuu, q, r, lb, ub)]
+    du, dx, mu = np.zeros(N), np.zeros((N + 1) * 3), np.zeros(N * 3)
+    nul, nuu = np.zeros(N), np.zeros(N)
+    it = C.c_int()
+    st = L.or_qp3_solve(N, *[_p(a) for a in ins], _p(du), _p(dx), _p(mu), _p(nul), _p(nuu),
+                        C.byref(it))
+    return dict(status=st, iters=it.value, du=du, dx=dx.reshape(N + 1, 3), mu=mu.reshape(N, 3),
+                nul=nul, nuu=nuu)
+
+
+def bfgs_blockn(W, s, y):
+    L = lib()
+    W = _arr(W).copy()
+    n = W.shape[0]
+    Wf = W.reshape(n * n).copy()
+    L.or_bfgs_blockn(n, _p(Wf), _p(_arr(s).copy()), _p(_arr(y).copy()))
+    return Wf.reshape(n, n)
+
+
+def sqp3(model: dict, ctrl: dict, EaR: float, x0, zbar, u, x, lam=None, pil=None, piu=None):
+    """One three-state OCP.  x0 (3), zbar (N+1), u (N), x ((N+1) x 3) scaled."""
+    L = lib()
+    m, c = make_model(model), make_ctrl(dict(ctrl, nx_model=3))
+    N = c.N
+    u = _arr(u).copy()
+    x = _arr(x).reshape((N + 1) * 3).copy()
+    lam = np.zeros(N * 3) if lam is None else _arr(lam).reshape(N * 3).copy()
+    pil = np.zeros(N) if pil is None else _arr(pil).copy()
+    piu = np.zeros(N) if piu is None else _arr(piu).copy()
+    zb = _arr(zbar).copy()
+    x0 = _arr(x0).copy()
+    info = SqpInfo()
+    L.or_sqp3(C.byref(m), C.byref(c), EaR, _p(x0), _p(zb), _p(u), _p(x), _p(lam), _p(pil),
+              _p(piu), C.byref(info))
+    d = {f: getattr(info, f) for f, _ in SqpInfo._fields_ if f != "pad0"}
+    return u, x.reshape(N + 1, 3), lam.reshape(N, 3), pil, piu, d

@@ -63,8 +63,24 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
   double zb[OR_MAX_N + 1];
   double F_prev = 0.0;
   double Ihat = 0.0;
+  /* three-state NMPC model: estimate of n, its 3x3 covariance, and the
+   * warm start with three states and three multipliers per stage */
+  const int nx3 = (c->kind == 0 && c->nx_model == 3);
+  double xh3[3] = {m->cA_in * m->V, m->cB_in * m->V, m->T_in * m->V};
+  double P3[9] = {c->P0, 0.0, 0.0, 0.0, c->P0, 0.0, 0.0, 0.0, c->P0};
+  static __thread double x3[(OR_MAX_N + 1) * 3], lam3[OR_MAX_N * 3];
 
-  if (c->kind == 0) {
+  if (nx3) {
+    double v0 = or_Fss(m, EaR_c, or_zbar(m, m->t0)) / Fconv;
+    v0 = fmin(fmax(v0, c->u_min / c->u_scale), c->u_max / c->u_scale);
+    for (int k = 0; k < N; ++k) {
+      u[k] = v0;
+      pil[k] = piu[k] = 0.0;
+      for (int q = 0; q < 3; ++q) lam3[k * 3 + q] = 0.0;
+    }
+    for (int k = 0; k <= N; ++k)
+      for (int q = 0; q < 3; ++q) x3[k * 3 + q] = xh3[q] / c->x_scale;
+  } else if (c->kind == 0) {
     /* first OCP guess: steady-state input of the first set-point (clipped),
      * states at the initial estimate, multipliers zero */
     double v0 = or_Fss(m, EaR_c, or_zbar(m, m->t0)) / Fconv;
@@ -80,7 +96,10 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
   for (int i = 0; i <= K; ++i) {
     const double t_i = m->t0 + (double)i * m->Ts;
     const double cT = n[2] / m->V;
-    if (!isfinite(cT) || !isfinite(xhat) || !isfinite(P)) {
+    int bad3 = 0;
+    for (int q = 0; q < 3 && nx3; ++q) bad3 |= !isfinite(xh3[q]);
+    for (int q = 0; q < 9 && nx3; ++q) bad3 |= !isfinite(P3[q]);
+    if (!isfinite(cT) || !isfinite(xhat) || !isfinite(P) || bad3) {
       out->nonfinite = 1;
       phi = NAN;
       break;
@@ -95,7 +114,34 @@ void or_traj(const or_model* m, const or_ctrl* c_in, uint64_t seed, int64_t j,
     const double zbar_i = or_zbar(m, t_i);
     double F;
     double its = 0.0;
-    if (c->kind == 0) {
+    if (nx3) {
+      /* three-state CD-EKF and OCP, as below */
+      if (i > 0) or_ekf3_predict(m, EaR_c, c->n_rk4, F_prev, xh3, P3);
+      or_ekf3_filter(m, y, xh3, P3, NULL);
+      for (int k = 1; k <= N; ++k) zb[k] = or_zbar(m, m->t0 + (double)(i + k) * m->Ts);
+      double x0s[3] = {xh3[0] / c->x_scale, xh3[1] / c->x_scale, xh3[2] / c->x_scale};
+      or_sqp_info info;
+      or_sqp3(m, c, EaR_c, x0s, zb, u, x3, lam3, pil, piu, &info);
+      out->n_ocp++;
+      out->sqp_iters += info.iters;
+      out->ls_trials += info.ls_trials;
+      out->n_hess_reset += info.n_hess_reset;
+      out->qp_iters += info.qp_iters;
+      if (info.status == 1) out->n_ocp_failed++;
+      if (info.status == 2) out->n_ls_fail++;
+      its = info.iters;
+      F = u[0] * Fconv;
+      for (int k = 0; k < N - 1; ++k) {
+        u[k] = u[k + 1];
+        pil[k] = pil[k + 1];
+        piu[k] = piu[k + 1];
+        for (int q = 0; q < 3; ++q) {
+          x3[(k + 1) * 3 + q] = x3[(k + 2) * 3 + q];
+          lam3[k * 3 + q] = lam3[(k + 1) * 3 + q];
+        }
+      }
+      xhat = xh3[2];
+    } else if (c->kind == 0) {
       /* CD-EKF: prediction from t_{i-1} (none before the first sample), filtering */
       if (i > 0) or_ekf_predict(m, EaR_c, c->n_rk4, F_prev, &xhat, &P);
       or_ekf_filter(m, y, &xhat, &P, NULL);

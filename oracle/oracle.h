@@ -63,7 +63,8 @@ typedef struct {
   int32_t n_rk4;        /* classical RK4 steps per interval, N_c             */
   int32_t sqp_max_it;   /* SQP iteration limit                               */
   int32_t ls_max;       /* maximum number of step halvings                   */
-  int32_t pad0;
+  int32_t nx_model;     /* NMPC model: 0 or 1 = one-state (Sec. VI),
+                           3 = the three-state model of Eq. (CSTR)           */
   double u_min, u_max;  /* input bounds (mL/min)                             */
   double kP, kI, kaw;   /* PI gains, acting on F in L/s and e in K           */
   double Qz;            /* output weight of the NMPC objective               */
@@ -158,6 +159,23 @@ void or_traj(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j,
              or_traj_out* out, double* trace);
 void or_run(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j0,
             int64_t j1, int n_threads, or_traj_out* out);
+
+/* ---- three-state NMPC model (or_nmpc3.c) ---- */
+void or_drift3(const or_model* m, double EaR, double T_in, const double n[3], double F,
+               double f[3], double J[9], double fF[3]);
+void or_rk4_interval3(const or_model* m, double EaR, int n_rk4, double Ts, const double x0[3],
+                      double v, double Fconv, double xF[3], double A[9], double B[3]);
+void or_ekf3_predict(const or_model* m, double EaR, int n_rk4, double F, double x[3],
+                     double P[9]);
+void or_ekf3_filter(const or_model* m, double y, double x[3], double P[9], double* P_short);
+int or_qp3_solve(int N, const double* A, const double* B, const double* b, const double* Wxx,
+                 const double* Wxu, const double* Wuu, const double* q, const double* r,
+                 const double* lb, const double* ub, double* du, double* dx, double* mu,
+                 double* nul, double* nuu, int* iters);
+void or_bfgs_blockn(int n, double* W, const double* s, const double* y);
+int or_sqp3(const or_model* m, const or_ctrl* c, double EaR, const double x0[3],
+            const double* zbar, double* u, double* x, double* lam, double* pil, double* piu,
+            or_sqp_info* info);
 
 /* ---- derivatives of Phi_j with respect to the PI gains (or_grad.c) ---- */
 /* Complex-step derivative of Phi_j with respect to gain `which` (0 = k_P,
