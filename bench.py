@@ -55,6 +55,14 @@ OPS_EKF = 5 * (4 * (20 + W_EXP + W_DIV) + 12) + 12 + W_DIV   # predict (N_c = 5)
 OPS_EM = 38 + W_EXP + W_DIV - 5.6 + 12 + 2 * (8 + W_LOG + W_SQRT + W_SINCOS)  # substep
 PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
 
+# DRAM bytes (read + write) of k_nmpc_persist<double> per control step of the
+# 30,000-trajectory FP64 study, from one ncu capture of a 60-step case of it
+# (dram__bytes_read.sum 49.13 GB + dram__bytes_write.sum 75.06 GB; the
+# scratch traffic grows with the steps: 1.96 GB/step on an earlier 120-step
+# capture).  A full launch is scaled by its steps and trajectories.
+TRAFFIC_WORKLOAD = "cstr_30k_x240_N20_fp64"
+TRAFFIC_BYTES_PER_STEP_30K = (49125386752 + 75058529024) / 60
+
 
 def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st):
     """FP64 pipe operations of one NMPC launch from the counters it reports."""
@@ -299,8 +307,14 @@ def main():
     flops = nmpc_flops(w["model"], w["nmpc"], T, st_n)
     k_ms = statistics.mean(nmpc_ms)
     achieved = flops / (k_ms / 1e3) / 1e12
+    traffic = None
+    if (args.workload == TRAFFIC_WORKLOAD and w["nmpc"].get("schedule") == "persistent"
+            and w["nmpc"]["precision"] == "fp64"):
+        traffic = TRAFFIC_BYTES_PER_STEP_30K * w["model"]["n_steps"] * T / 30000.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch, scaled from a 60-step ncu capture; "
+                                "structure-of-arrays scratch, not algorithmic bytes",
                 "kernel": "k_nmpc_persist<double> (FP64 pipe)",
                 "work": "FP64 pipe operations x 2 (DFMA-equivalent flops), elementary "
                         "functions weighted by their measured DFMA cost",

@@ -116,6 +116,10 @@ typedef struct {
   int32_t schedule;       /* mc_schedule                                       */
   int32_t threads_per_sm; /* persistent schedule: resident threads per SM,
                              0 = one per trajectory up to the GPU's capacity   */
+  int32_t nx_model;       /* NMPC model: 0 or 1 = the one-state model of Sec. VI
+                             (the paper's); 3 = the three-state model of
+                             Eq. (CSTR) with a 3x3 CD-EKF (FP64, active-set
+                             QP, static schedule)                             */
 } mc_controller_t;
 
 typedef enum {

@@ -23,6 +23,7 @@
 #include "mc_closedloop.cuh"
 #include "mc_grad.cuh"
 #include "mc_qp_par.cuh"
+#include "mc_nmpc3.cuh"
 
 namespace mc {
 
@@ -38,6 +39,22 @@ __global__ void __launch_bounds__(32) k_nmpc(DevModel m, DevCtrl c, int64_t j0, 
   const Ws w{ws + t, ld, c.N + 1};
   for (int64_t j = j0 + t; j < j1; j += ld) {
     const TrajOut o = traj_nmpc<R>(m, c, (uint32_t)j, w);
+    phi[j] = o.phi;
+#pragma unroll
+    for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
+  }
+}
+
+// The three-state NMPC closed loop (FP64, static schedule).
+__global__ void __launch_bounds__(32) k_nmpc3(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
+                                              double* __restrict__ phi,
+                                              int32_t* __restrict__ cnt, double* ws,
+                                              int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ld) return;
+  const Ws w{ws + t, ld, c.N + 1};
+  for (int64_t j = j0 + t; j < j1; j += ld) {
+    const TrajOut o = traj_nmpc3(m, c, (uint32_t)j, w);
     phi[j] = o.phi;
 #pragma unroll
     for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
@@ -487,6 +504,13 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
       return bad("unknown schedule");
     if (cc->threads_per_sm < 0 || cc->threads_per_sm > 2048)
       return bad("threads_per_sm must be 0..2048");
+    if (cc->nx_model != 0 && cc->nx_model != 1 && cc->nx_model != 3)
+      return bad("nx_model must be 0, 1 or 3");
+    if (cc->nx_model == 3 &&
+        (cc->precision != MC_FP64 || cc->qp_solver != MC_QP_ACTIVE_SET ||
+         cc->schedule != MC_SCHED_STATIC))
+      return bad("the three-state NMPC runs in FP64 with the active-set QP and the static "
+                 "schedule");
   }
   memset(m, 0, sizeof(*m));
   m->V = mm->V; m->k0 = mm->k0; m->EaR = mm->EaR; m->beta = mm->beta;
@@ -513,6 +537,7 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   c->Qz = cc->Qz; c->P0 = cc->P0; c->sqp_tol = cc->sqp_tol; c->ip_tol = cc->ip_tol;
   c->u_scale = cc->u_scale; c->x_scale = cc->x_scale;
   c->N_min = cc->N_min; c->it_min = cc->sqp_max_it_min;
+  c->nx_model = (cc->kind == MC_CTRL_NMPC && cc->nx_model == 3) ? 3 : 1;
   if (cc->kind == MC_CTRL_NMPC) {
     c->Fconv = cc->u_scale / 60000.0;
     c->vmin = cc->u_min / cc->u_scale;
@@ -529,16 +554,18 @@ static bool to_dev(T** d, const T* h, size_t n) {
   return true;
 }
 
-static int64_t nmpc_threads_for(int64_t n) {
+static int64_t nmpc_threads_for(int64_t n, int nx_model) {
   // every trajectory gets its own thread while they fit on the GPU at once
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nmpc<double>, kNmpcThreads, 0) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 4;
+  const cudaError_t oe =
+      (nx_model == 3)
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nmpc3, kNmpcThreads, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nmpc<double>, kNmpcThreads,
+                                                          0);
+  if (oe != cudaSuccess || per_sm < 1) per_sm = 4;
   const int64_t cap = (int64_t)sms * per_sm * kNmpcThreads;
   // equal numbers of trajectories per thread when they exceed the resident threads
   const int64_t passes = (n + cap - 1) / cap;
@@ -611,8 +638,9 @@ mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl, int64_
             alloc((void**)&h->part, sizeof(Partial) * kMaxStatBlocks) &&
             alloc((void**)&h->dstats, sizeof(DevStats));
   if (ok && h->c.kind == MC_CTRL_NMPC && n_sims > 0) {
-    h->ws_ld = nmpc_threads_for(n_sims);
-    const size_t words = (size_t)kNArr * (h->c.N + 1) * (size_t)h->ws_ld;
+    h->ws_ld = nmpc_threads_for(n_sims, h->c.nx_model);
+    const size_t words =
+        (size_t)(h->c.nx_model == 3 ? (int)kNArr3 : (int)kNArr) * (h->c.N + 1) * (size_t)h->ws_ld;
     ok = alloc((void**)&h->ws, words * sizeof(double)) &&
          alloc((void**)&h->next, sizeof(unsigned long long));
     int dev = 0, sms = 152;
@@ -707,7 +735,10 @@ static mc_status enqueue_run(mc_handle* h, const DevModel& m, int64_t j0, int64_
       int64_t threads = n < h->ws_ld ? n : h->ws_ld;
       const int64_t blocks = (threads + kNmpcThreads - 1) / kNmpcThreads;
       // the scratch stride is the allocation's, the thread count the range's
-      if (h->c.precision == MC_FP64)
+      if (h->c.nx_model == 3)
+        k_nmpc3<<<(unsigned)blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, j1, h->phi, h->cnt,
+                                                           h->ws, h->ws_ld);
+      else if (h->c.precision == MC_FP64)
         k_nmpc<double><<<(unsigned)blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, j1, h->phi,
                                                                   h->cnt, h->ws, h->ws_ld);
       else

@@ -38,6 +38,7 @@ struct DevCtrl {
   int kind, precision, N, n_rk4;
   int sqp_max_it, ls_max, qp_solver, ip_max_it;
   int N_min, it_min;   // > 0: per-trajectory N in [N_min, N], limit in [it_min, sqp_max_it]
+  int nx_model;        // NMPC model: 1 = one-state, 3 = three-state
   double u_min, u_max, kP, kI, kaw, Qz, P0, sqp_tol, ip_tol, u_scale, x_scale;
   double Fconv;        // OCP input unit -> L/s
   double vmin, vmax;   // input bounds in OCP units

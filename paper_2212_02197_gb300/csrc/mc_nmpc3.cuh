@@ -1,0 +1,779 @@
+// mc_nmpc3.cuh -- the NMPC with the three-state model of Eq. (CSTR): CD-EKF
+// on n = (n_A, n_B, n_T) with a 3x3 covariance, multiple-shooting OCP with
+// three states and one input per stage, the SQP of Sec. IV (Riccati active-
+// set QP with a 3x3 Riccati matrix, l1-merit line search, damped BFGS on
+// 1/4/3-dimensional blocks, scaled convergence test).  FP64, one thread per
+// trajectory.
+//
+// Scratch: structure of arrays as for the one-state NMPC, one array per
+// component: w(X0 + i, k) is component i of x_k, symmetric 3x3 matrices keep
+// their six entries (00, 01, 02, 11, 12, 22), A_k its nine (row-major).
+#pragma once
+
+#include "mc_closedloop.cuh"
+
+namespace mc {
+
+enum Arr3 : int {
+  U3 = 0, X3 = 1 /* 3 */, LAM3 = 4 /* 3 */, PIL3 = 7, PIU3 = 8,
+  WXX3 = 9 /* 6 */, WXU3 = 15 /* 3 */, WUU3 = 18,
+  EA3 = 19 /* 9 */, EB3 = 28 /* 3 */, EG3 = 31 /* 3 */, EQ3 = 34,  // q_k: temperature part
+  TA3 = 35 /* 9 */, TB3 = 44 /* 3 */, TG3 = 47 /* 3 */, TQ3 = 50, UT3 = 51, XT3 = 52 /* 3 */,
+  DU3 = 55, DX3 = 56 /* 3 */, MU3 = 59 /* 3 */, NUL3 = 62, NUU3 = 63,
+  SIG3 = 64 /* 3 */, GLU3 = 67, GLX3 = 68 /* 3 */, ZB3 = 71, LB3 = 72, UB3 = 73,
+  RP3 = 74 /* 6 */, RPP3 = 80 /* 3 */, RK3 = 83 /* 3 */, RKF3 = 86, RZ3 = 87,
+  kNArr3 = 88
+};
+
+// index of entry (i, j) of a symmetric 3x3 matrix stored as 00 01 02 11 12 22
+__host__ __device__ constexpr int s3(int i, int j) {
+  return (i <= j) ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
+}
+
+// ---------------------------------------------------------------------------
+// Model: drift of Eq. (CSTR), its Jacobian J = df/dn and df/dF.
+__device__ __forceinline__ void drift3(const DevModel& m, double EaR, double T_in,
+                                       const double n[3], double F, double f[3], double J[9],
+                                       double fF[3]) {
+  const double V = m.V;
+  const double cA = n[0] / V, cB = n[1] / V, cT = n[2] / V;
+  const double k = m.k0 * expr(-EaR / cT);
+  const double rV = k * cA * cB * V;
+  const double S[3] = {-1.0, -2.0, m.beta};
+  const double cin[3] = {m.cA_in, m.cB_in, T_in};
+  const double c[3] = {cA, cB, cT};
+  const double drv[3] = {k * cB, k * cA, rV * EaR / (cT * cT) / V};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    f[p] = cin[p] * F - c[p] * F + S[p] * rV;
+    fF[p] = cin[p] - c[p];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) J[p * 3 + q] = (p == q ? -F / V : 0.0) + S[p] * drv[q];
+  }
+}
+
+// F(x0, v) over Ts by n_rk4 RK4 steps of the drift (nominal T_in) and the
+// sensitivities A = dF/dx0, B = dF/dv from the same RK4 steps applied to the
+// variational equations.  States in moles, v in OCP units.
+__device__ __noinline__ void rk4_interval3(const DevModel& m, double EaR, int n_rk4, double Ts,
+                                           const double* x0, double v, double Fconv,
+                                           double* xF, double* A, double* B) {
+  const double h = Ts / (double)n_rk4;
+  const double F = v * Fconv;
+  double x[3], Phi[9], psi[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    x[i] = x0[i];
+    psi[i] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Phi[i * 3 + j] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int s = 0; s < n_rk4; ++s) {
+    double ax[3] = {0, 0, 0}, aP[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, ap[3] = {0, 0, 0};
+    double kx[3], kP[9], kp[3];
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const double a = (st == 0) ? 0.0 : ((st == 3) ? h : 0.5 * h);
+      double xs[3], Ps[9], ps[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        xs[i] = x[i] + (st ? a * kx[i] : 0.0);
+        ps[i] = psi[i] + (st ? a * kp[i] : 0.0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Ps[i * 3 + j] = Phi[i * 3 + j] + (st ? a * kP[i * 3 + j] : 0.0);
+      }
+      double f[3], J[9], fF[3];
+      drift3(m, EaR, m.T_in, xs, F, f, J, fF);
+      const double wgt = (st == 0 || st == 3) ? 1.0 : 2.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        kx[i] = f[i];
+        double sp = fF[i] * Fconv;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sp += J[i * 3 + q] * ps[q];
+        kp[i] = sp;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          double sP = 0.0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) sP += J[i * 3 + q] * Ps[q * 3 + j];
+          kP[i * 3 + j] = sP;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        ax[i] += wgt * kx[i];
+        ap[i] += wgt * kp[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) aP[i] += wgt * kP[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x[i] = x[i] + h / 6.0 * ax[i];
+      psi[i] = psi[i] + h / 6.0 * ap[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Phi[i] = Phi[i] + h / 6.0 * aP[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    xF[i] = x[i];
+    B[i] = psi[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A[i] = Phi[i];
+}
+
+// CD-EKF prediction for three states (P symmetric, six entries).
+__device__ void ekf3_predict(const DevModel& m, double EaR, int n_rk4, double F, double x[3],
+                             double P[6]) {
+  const double h = m.Ts / (double)n_rk4;
+  double Qd[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Qd[i] = F * F * m.sigma[i] * m.sigma[i];
+  for (int s = 0; s < n_rk4; ++s) {
+    double ax[3] = {0, 0, 0}, aP[6] = {0, 0, 0, 0, 0, 0};
+    double kx[3], kP[6];
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const double a = (st == 0) ? 0.0 : ((st == 3) ? h : 0.5 * h);
+      double xs[3], Ps[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) xs[i] = x[i] + (st ? a * kx[i] : 0.0);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) Ps[i] = P[i] + (st ? a * kP[i] : 0.0);
+      double f[3], J[9], fF[3];
+      drift3(m, EaR, m.T_in, xs, F, f, J, fF);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) kx[i] = f[i];
+      // J P + P J^T + Q, entry (i, j), i <= j
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+          double v = (i == j) ? Qd[i] : 0.0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) v += J[i * 3 + q] * Ps[s3(q, j)] + Ps[s3(i, q)] * J[j * 3 + q];
+          kP[s3(i, j)] = v;
+        }
+      const double wgt = (st == 0 || st == 3) ? 1.0 : 2.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ax[i] += wgt * kx[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) aP[i] += wgt * kP[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x[i] = x[i] + h / 6.0 * ax[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) P[i] = P[i] + h / 6.0 * aP[i];
+  }
+}
+
+// Filtering with y = n_T / V + v, Joseph form.
+__device__ void ekf3_filter(const DevModel& m, double y, double x[3], double P[6]) {
+  const double R = m.meas_sd * m.meas_sd;
+  const double iV = 1.0 / m.V;
+  double PC[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) PC[i] = P[s3(i, 2)] * iV;
+  const double Re = R + iV * PC[2];
+  double K[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) K[i] = PC[i] / Re;
+  const double e = y - x[2] * iV;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x[i] = x[i] + K[i] * e;
+  // M = I - K C (C = [0 0 1/V]); P = M P M^T + K R K^T
+  double M[9], MP[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i * 3 + j] = (i == j ? 1.0 : 0.0) - (j == 2 ? K[i] * iV : 0.0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s += M[i * 3 + q] * P[s3(q, j)];
+      MP[i * 3 + j] = s;
+    }
+  double Pn[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s += MP[i * 3 + q] * M[j * 3 + q];
+      Pn[s3(i, j)] = s + K[i] * R * K[j];
+    }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) P[i] = Pn[i];
+}
+
+// ---------------------------------------------------------------------------
+// QP subproblem with three states per stage: Riccati recursion with P_{k+1}
+// (3x3), p_{k+1}, K_k (1x3), k_k inside the primal active-set method of
+// qp_active_set (same working-set rules).  Reads EA3, EB3, EG3 (b_k), WXX3,
+// WXU3, WUU3, EQ3 (temperature part of q_k), LB3, UB3; writes DU3, DX3, MU3,
+// NUL3, NUU3.  q_k and r_k are zero except the temperature part of q_k.
+
+__device__ bool riccati3(const Ws& w, int N, uint64_t fixed) {
+  double P[6], p[3];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) P[i] = w(WXX3 + i, N);
+  p[0] = 0.0;
+  p[1] = 0.0;
+  p[2] = w(EQ3, N);
+  for (int k = N - 1; k >= 0; --k) {
+    double A[9], B[3], b[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A[i] = (k > 0) ? w(EA3 + i, k) : 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      B[i] = w(EB3 + i, k);
+      b[i] = w(EG3 + i, k);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) w(RP3 + i, k + 1) = P[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w(RPP3 + i, k + 1) = p[i];
+    // Pbp = P b + p, PB = P B
+    double Pbp[3], PB[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double s1 = p[i], s2 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        s1 += P[s3(i, q)] * b[q];
+        s2 += P[s3(i, q)] * B[q];
+      }
+      Pbp[i] = s1;
+      PB[i] = s2;
+    }
+    // A^T P A (symmetric)
+    double AtPA[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) s += A[a * 3 + i] * P[s3(a, c2)] * A[c2 * 3 + j];
+        AtPA[s3(i, j)] = s;
+      }
+    double Pn[6], pn[3];
+    const double q2 = (k > 0) ? w(EQ3, k) : 0.0;
+    if ((fixed >> k) & 1ull) {
+      const double c = w(DU3, k);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w(RK3 + i, k) = 0.0;
+      w(RKF3, k) = c;
+      // p_k = q_k + Wxu c + A^T (P (B c + b) + p)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double s = (i == 2 ? q2 : 0.0) + ((k > 0) ? w(WXU3 + i, k) * c : 0.0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s += A[a * 3 + i] * (PB[a] * c + Pbp[a]);
+        pn[i] = s;
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) Pn[i] = ((k > 0) ? w(WXX3 + i, k) : 0.0) + AtPA[i];
+    } else {
+      double Rb = w(WUU3, k);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Rb += B[q] * PB[q];
+      if (!(Rb > 0.0)) return false;
+      const double iR = 1.0 / Rb;
+      double Sb[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double s = (k > 0) ? w(WXU3 + i, k) : 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s += A[a * 3 + i] * PB[a];
+        Sb[i] = (k > 0) ? s : 0.0;
+      }
+      double sb = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) sb += B[q] * Pbp[q];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w(RK3 + i, k) = -Sb[i] * iR;
+      w(RKF3, k) = -sb * iR;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double s = (i == 2 ? q2 : 0.0) - Sb[i] * sb * iR;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s += A[a * 3 + i] * Pbp[a];
+        pn[i] = s;
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j)
+          Pn[s3(i, j)] = ((k > 0) ? w(WXX3 + s3(i, j), k) : 0.0) + AtPA[s3(i, j)] -
+                         Sb[i] * Sb[j] * iR;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) P[i] = Pn[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p[i] = pn[i];
+  }
+  return true;
+}
+
+__device__ QpResult qp3_active_set(const Ws& w, int N, int max_it) {
+  uint64_t lo = 0, up = 0;
+  double gscale = 1.0;
+  for (int k = 0; k < N; ++k) {
+    const double lb = w(LB3, k), ub = w(UB3, k);
+    double du = 0.0;
+    if (lb >= 0.0) {
+      lo |= 1ull << k;
+      du = lb;
+    } else if (ub <= 0.0) {
+      up |= 1ull << k;
+      du = ub;
+    }
+    w(DU3, k) = du;
+    gscale = fmax(gscale, fabs(w(EQ3, k + 1)));
+  }
+  const double mult_tol = 1e-13 * gscale;
+  QpResult res{0, 1};
+  for (int it = 0; it < max_it; ++it) {
+    res.iters = it + 1;
+    const uint64_t fixed = lo | up;
+    if (!riccati3(w, N, fixed)) {
+      res.status = 2;
+      return res;
+    }
+    double dx[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < N; ++k) {
+      double z = w(RKF3, k);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) z += w(RK3 + i, k) * dx[i];
+      double dxn[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double s = w(EB3 + i, k) * z + w(EG3 + i, k);
+        if (k > 0)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) s += w(EA3 + i * 3 + q, k) * dx[q];
+        dxn[i] = s;
+      }
+      w(RZ3, k) = z;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        w(DX3 + i, k + 1) = dxn[i];
+        double s = w(RPP3 + i, k + 1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s += w(RP3 + s3(i, q), k + 1) * dxn[q];
+        w(MU3 + i, k) = -s;
+        dx[i] = dxn[i];
+      }
+    }
+    double alpha = 1.0;
+    int block = -1;
+    bool block_lo = false;
+    for (int k = 0; k < N; ++k) {
+      if ((fixed >> k) & 1ull) continue;
+      const double z = w(RZ3, k), du = w(DU3, k);
+      const double lb = w(LB3, k), ub = w(UB3, k);
+      const double pk = z - du;
+      if (pk < 0.0 && z < lb) {
+        const double t = (lb - du) / pk;
+        if (t < alpha) { alpha = t; block = k; block_lo = true; }
+      } else if (pk > 0.0 && z > ub) {
+        const double t = (ub - du) / pk;
+        if (t < alpha) { alpha = t; block = k; block_lo = false; }
+      }
+    }
+    if (block >= 0) {
+      if (alpha < 0.0) alpha = 0.0;
+      for (int k = 0; k < N; ++k) {
+        if ((fixed >> k) & 1ull) continue;
+        const double du = w(DU3, k);
+        w(DU3, k) = du + alpha * (w(RZ3, k) - du);
+      }
+      if (block_lo) {
+        lo |= 1ull << block;
+        w(DU3, block) = w(LB3, block);
+      } else {
+        up |= 1ull << block;
+        w(DU3, block) = w(UB3, block);
+      }
+      continue;
+    }
+    int worst = -1;
+    double worst_val = -mult_tol;
+    for (int k = 0; k < N; ++k) {
+      const bool f = (fixed >> k) & 1ull;
+      const double du = f ? w(DU3, k) : w(RZ3, k);
+      w(DU3, k) = du;
+      if (!f) continue;
+      double v = w(WUU3, k) * du;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (k > 0) v += w(WXU3 + i, k) * w(DX3 + i, k);
+        v -= w(MU3 + i, k) * w(EB3 + i, k);
+      }
+      const double lam = ((lo >> k) & 1ull) ? v : -v;
+      if (lam < worst_val) { worst_val = lam; worst = k; }
+    }
+    if (worst < 0) {
+      res.status = 0;
+      break;
+    }
+    lo &= ~(1ull << worst);
+    up &= ~(1ull << worst);
+  }
+  for (int k = 0; k < N; ++k) {
+    double nl = 0.0, nu = 0.0;
+    if (((lo | up) >> k) & 1ull) {
+      double v = w(WUU3, k) * w(DU3, k);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (k > 0) v += w(WXU3 + i, k) * w(DX3 + i, k);
+        v -= w(MU3 + i, k) * w(EB3 + i, k);
+      }
+      if ((lo >> k) & 1ull) nl = v; else nu = -v;
+    }
+    w(NUL3, k) = nl;
+    w(NUU3, k) = nu;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) w(DX3 + i, 0) = 0.0;
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// SQP for the three-state OCP.
+
+// Shooting of all intervals at (u_arr, x_arr) with sensitivities into
+// (a_arr, b_arr, g_arr) and the temperature part of q into q_arr; returns f.
+__device__ __noinline__ double evaluate3(const DevModel& m, const DevCtrl& c, double EaR, int N,
+                                         const Ws& w, int u_arr, int x_arr, int a_arr,
+                                         int b_arr, int g_arr, int q_arr) {
+  const double xs = c.x_scale;
+  double f = 0.0;
+  for (int k = 0; k < N; ++k) {
+    double n0[3], Fn[3], A[9], B[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n0[i] = ((k == 0) ? w(X3 + i, 0) : w(x_arr + i, k)) * xs;
+    rk4_interval3(m, EaR, c.n_rk4, m.Ts, n0, w(u_arr, k), c.Fconv, Fn, A, B);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      w(b_arr + i, k) = B[i] / xs;
+      w(g_arr + i, k) = Fn[i] / xs - w(x_arr + i, k + 1);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) w(a_arr + i, k) = A[i];
+  }
+  w(q_arr, 0) = 0.0;
+  for (int k = 1; k <= N; ++k) {
+    const double dz = w(x_arr + 2, k) * xs / m.V - w(ZB3, k);
+    f += c.Qz * dz * dz * m.Ts;
+    w(q_arr, k) = 2.0 * c.Qz * dz * m.Ts * xs / m.V;
+  }
+  return f;
+}
+
+// damped BFGS of an n x n symmetric block held in registers (n <= 4)
+__device__ __forceinline__ void bfgs_blockn(int n, double* W, const double* s, const double* y) {
+  const double eps_m = 2.220446049250313e-16;
+  double Ws[4], rr[4];
+  double sWs = 0.0, sy = 0.0, sr = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double t = 0.0;
+    for (int j = 0; j < n; ++j) t += W[i * 4 + j] * s[j];
+    Ws[i] = t;
+    sWs += s[i] * t;
+    sy += s[i] * y[i];
+  }
+  const double theta = (sy >= 0.2 * sWs) ? 1.0 : (0.8 * sWs) / (sWs - sy);
+  for (int i = 0; i < n; ++i) {
+    rr[i] = theta * y[i] + (1.0 - theta) * Ws[i];
+    sr += s[i] * rr[i];
+  }
+  if (!(fmin(sWs, sr) > eps_m)) return;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      W[i * 4 + j] = W[i * 4 + j] - Ws[i] * Ws[j] / sWs + rr[i] * rr[j] / sr;
+}
+
+__device__ __forceinline__ bool chol_pd(int n, const double* W) {
+  double a[16];
+  for (int i = 0; i < 16; ++i) a[i] = W[i];
+  for (int j = 0; j < n; ++j) {
+    double d = a[j * 4 + j];
+    for (int k = 0; k < j; ++k) d -= a[j * 4 + k] * a[j * 4 + k];
+    if (!(d > 0.0)) return false;
+    d = sqrt(d);
+    a[j * 4 + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = a[i * 4 + j];
+      for (int k = 0; k < j; ++k) s -= a[i * 4 + k] * a[j * 4 + k];
+      a[i * 4 + j] = s / d;
+    }
+  }
+  return true;
+}
+
+// W blocks in the scratch as 4x4 (stage k = 1..N-1: x then u), W_0 = [u],
+// W_N = [x]; load / store them through these helpers.
+__device__ __forceinline__ void load_block(const Ws& w, int k, int N, double* W) {
+  for (int i = 0; i < 16; ++i) W[i] = 0.0;
+  if (k == 0) {
+    W[0] = w(WUU3, 0);
+    return;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) W[i * 4 + j] = w(WXX3 + s3(i, j), k);
+  if (k < N) {
+    for (int i = 0; i < 3; ++i) W[i * 4 + 3] = W[3 * 4 + i] = w(WXU3 + i, k);
+    W[15] = w(WUU3, k);
+  }
+}
+__device__ __forceinline__ void store_block(const Ws& w, int k, int N, const double* W) {
+  if (k == 0) {
+    w(WUU3, 0) = W[0];
+    return;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) w(WXX3 + s3(i, j), k) = W[i * 4 + j];
+  if (k < N) {
+    for (int i = 0; i < 3; ++i) w(WXU3 + i, k) = W[i * 4 + 3];
+    w(WUU3, k) = W[15];
+  }
+}
+__device__ __forceinline__ void identity_blocks(const Ws& w, int N) {
+  for (int k = 0; k <= N; ++k) {
+    for (int i = 0; i < 6; ++i) w(WXX3 + i, k) = (i == 0 || i == 3 || i == 5) ? 1.0 : 0.0;
+    for (int i = 0; i < 3; ++i) w(WXU3 + i, k) = 0.0;
+    w(WUU3, k) = 1.0;
+  }
+}
+
+// Gradient of the Lagrangian at the evaluation in (EA3, EB3, EQ3):
+//   gu_k = -lam_k^T B_k - pil_k + piu_k, gx_k = q_k - A_k^T lam_k + lam_{k-1}.
+__device__ __forceinline__ double lagr_gu(const Ws& w, int k) {
+  double s = -w(PIL3, k) + w(PIU3, k);
+  for (int i = 0; i < 3; ++i) s -= w(LAM3 + i, k) * w(EB3 + i, k);
+  return s;
+}
+__device__ __forceinline__ double lagr_gx(const Ws& w, int k, int N, int i) {
+  double s = (i == 2 ? w(EQ3, k) : 0.0) + w(LAM3 + i, k - 1);
+  if (k < N)
+    for (int a = 0; a < 3; ++a) s -= w(EA3 + a * 3 + i, k) * w(LAM3 + a, k);
+  return s;
+}
+
+// The SQP of Sec. IV for one three-state OCP from the warm start in (U3, X3,
+// LAM3, PIL3, PIU3) with x_0 in X3(., 0) and the set-points in ZB3.
+__device__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, double EaR, const Ws& w,
+                              int N, int max_it) {
+  const double c1 = 1e-4, s_max = 100.0;
+  SqpInfo info{};
+  identity_blocks(w, N);
+  double f = evaluate3(m, c, EaR, N, w, U3, X3, EA3, EB3, EG3, EQ3);
+  double alpha = 0.0;
+  for (int l = 0;; ++l) {
+    if (l > 0) {
+      // damped block BFGS: s = alpha (du, dx), y = grad L at the new point
+      // minus grad L at the old point, both with the new multipliers
+      bool pd = true;
+      for (int k = 0; k <= N; ++k) {
+        double W[16], s[4], y[4];
+        load_block(w, k, N, W);
+        int n;
+        if (k == 0) {
+          n = 1;
+          s[0] = alpha * w(DU3, 0);
+          y[0] = lagr_gu(w, 0) - w(GLU3, 0);
+        } else {
+          for (int i = 0; i < 3; ++i) {
+            s[i] = alpha * w(DX3 + i, k);
+            y[i] = lagr_gx(w, k, N, i) - w(GLX3 + i, k);
+          }
+          n = 3;
+          if (k < N) {
+            s[3] = alpha * w(DU3, k);
+            y[3] = lagr_gu(w, k) - w(GLU3, k);
+            n = 4;
+          }
+        }
+        bfgs_blockn(n, W, s, y);
+        store_block(w, k, N, W);
+        pd = pd && chol_pd(n, W);
+      }
+      if (!pd) {
+        identity_blocks(w, N);
+        info.n_hess_reset++;
+      }
+    }
+    // scaled convergence test
+    double mult1 = 0.0, kg = 0.0, ke = 0.0;
+    for (int k = 0; k < N; ++k) {
+      mult1 += fabs(w(PIL3, k)) + fabs(w(PIU3, k));
+      for (int i = 0; i < 3; ++i) mult1 += fabs(w(LAM3 + i, k));
+      kg = fmax(kg, fabs(lagr_gu(w, k)));
+      for (int i = 0; i < 3; ++i) {
+        kg = fmax(kg, fabs(lagr_gx(w, k + 1, N, i)));
+        ke = fmax(ke, fabs(w(EG3 + i, k)));
+      }
+    }
+    const double s_d = fmax(s_max, mult1 / (5.0 * N)) / s_max;
+    kg /= s_d;
+    info.kkt_grad = kg;
+    info.kkt_eq = ke;
+    info.f = f;
+    if (kg <= c.sqp_tol && ke <= c.sqp_tol) {
+      info.status = 0;
+      break;
+    }
+    if (l >= max_it) {
+      info.status = 1;
+      break;
+    }
+    // QP at xi^[l]
+    for (int k = 0; k < N; ++k) {
+      const double u = w(U3, k);
+      w(LB3, k) = c.vmin - u;
+      w(UB3, k) = c.vmax - u;
+    }
+    const QpResult qr = qp3_active_set(w, N, 10 * N + 20);
+    info.qp_iters += qr.iters;
+    if (qr.status != 0) info.qp_fail++;
+    info.iters++;
+    double pen = 0.0, dfd = 0.0;
+    for (int k = 0; k < N; ++k)
+      for (int i = 0; i < 3; ++i) {
+        const double am = fabs(w(MU3 + i, k));
+        const double sg = (l == 0) ? am : fmax(am, 0.5 * (w(SIG3 + i, k) + am));
+        w(SIG3 + i, k) = sg;
+        pen += sg * fabs(w(EG3 + i, k));
+      }
+    for (int k = 1; k <= N; ++k) dfd += w(EQ3, k) * w(DX3 + 2, k);
+    const double T0 = f + pen, DT0 = dfd - pen;
+    // backtracking
+    alpha = 1.0;
+    bool accepted = false;
+    double ft = 0.0;
+    for (int hv = 0; hv <= c.ls_max; ++hv) {
+      for (int k = 0; k < N; ++k) {
+        w(UT3, k) = fmin(fmax(w(U3, k) + alpha * w(DU3, k), c.vmin), c.vmax);
+        for (int i = 0; i < 3; ++i) w(XT3 + i, k + 1) = w(X3 + i, k + 1) + alpha * w(DX3 + i, k + 1);
+      }
+      ft = evaluate3(m, c, EaR, N, w, UT3, XT3, TA3, TB3, TG3, TQ3);
+      info.ls_trials++;
+      double pt = 0.0;
+      for (int k = 0; k < N; ++k)
+        for (int i = 0; i < 3; ++i) pt += w(SIG3 + i, k) * fabs(w(TG3 + i, k));
+      if (ft + pt <= T0 + c1 * alpha * DT0) {
+        accepted = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    if (!accepted) {
+      info.status = 2;
+      break;
+    }
+    // multipliers, old-point gradient at the new multipliers, accept the point
+    for (int k = 0; k < N; ++k) {
+      for (int i = 0; i < 3; ++i)
+        w(LAM3 + i, k) = w(LAM3 + i, k) + alpha * (w(MU3 + i, k) - w(LAM3 + i, k));
+      w(PIL3, k) = w(PIL3, k) + alpha * (w(NUL3, k) - w(PIL3, k));
+      w(PIU3, k) = w(PIU3, k) + alpha * (w(NUU3, k) - w(PIU3, k));
+    }
+    for (int k = 0; k < N; ++k) {
+      w(GLU3, k) = lagr_gu(w, k);
+      for (int i = 0; i < 3; ++i) w(GLX3 + i, k + 1) = lagr_gx(w, k + 1, N, i);
+    }
+    for (int k = 0; k < N; ++k) {
+      const double un = w(UT3, k);
+      w(DU3, k) = (un - w(U3, k)) / alpha;
+      w(U3, k) = un;
+      for (int i = 0; i < 3; ++i) {
+        w(DX3 + i, k + 1) = (w(XT3 + i, k + 1) - w(X3 + i, k + 1)) / alpha;
+        w(X3 + i, k + 1) = w(XT3 + i, k + 1);
+        w(EB3 + i, k) = w(TB3 + i, k);
+        w(EG3 + i, k) = w(TG3 + i, k);
+      }
+      for (int i = 0; i < 9; ++i) w(EA3 + i, k) = w(TA3 + i, k);
+      w(EQ3, k + 1) = w(TQ3, k + 1);
+    }
+    f = ft;
+  }
+  return info;
+}
+
+// ---------------------------------------------------------------------------
+// Closed loop with the three-state NMPC (plant, measurement, Phi as in
+// traj_nmpc; FP64 only).
+__device__ TrajOut traj_nmpc3(const DevModel& m, const DevCtrl& c, uint32_t j, const Ws& w) {
+  TrajOut out{};
+  const TrajParams tp = traj_params(m, c, j);
+  const int N = tp.N, K = m.n_steps;
+  double n[3] = {m.cA_in * m.V, m.cB_in * m.V, m.T_in * m.V};
+  double xh[3] = {n[0], n[1], n[2]};
+  double P[6] = {c.P0, 0.0, 0.0, c.P0, 0.0, c.P0};
+  double v0 = Fss(m, tp.EaR_c, zbar(m, m.t0)) / c.Fconv;
+  v0 = fmin(fmax(v0, c.vmin), c.vmax);
+  for (int k = 0; k < N; ++k) {
+    w(U3, k) = v0;
+    w(PIL3, k) = 0.0;
+    w(PIU3, k) = 0.0;
+    for (int i = 0; i < 3; ++i) w(LAM3 + i, k) = 0.0;
+  }
+  for (int k = 0; k <= N; ++k)
+    for (int i = 0; i < 3; ++i) w(X3 + i, k) = xh[i] / c.x_scale;
+  double phi = 0.0, F_prev = 0.0;
+  for (int i = 0; i <= K; ++i) {
+    const double t_i = m.t0 + (double)i * m.Ts;
+    const double cT = n[2] / m.V;
+    bool bad = !isfinite(cT);
+    for (int q = 0; q < 3; ++q) bad = bad || !isfinite(xh[q]);
+    for (int q = 0; q < 6; ++q) bad = bad || !isfinite(P[q]);
+    if (bad) {
+      out.cnt[6] = 1;
+      out.phi = nan("");
+      return out;
+    }
+    const double ez = cT - zbar(m, t_i);
+    phi += ez * ez;
+    if (i == K) break;
+    const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
+    if (i > 0) ekf3_predict(m, tp.EaR_c, c.n_rk4, F_prev, xh, P);
+    ekf3_filter(m, y, xh, P);
+    for (int k = 1; k <= N; ++k) w(ZB3, k) = zbar(m, m.t0 + (double)(i + k) * m.Ts);
+    for (int q = 0; q < 3; ++q) w(X3 + q, 0) = xh[q] / c.x_scale;
+    const SqpInfo si = sqp3_solve(m, c, tp.EaR_c, w, N, tp.max_it);
+    out.cnt[0] += (si.status == 1);
+    out.cnt[1] += si.iters;
+    out.cnt[2] += si.ls_trials;
+    out.cnt[3] += si.n_hess_reset;
+    out.cnt[4] += (si.status == 2);
+    out.cnt[5] += si.qp_iters;
+    out.cnt[7] += si.qp_fail;
+    const double F = w(U3, 0) * c.Fconv;
+    for (int k = 0; k < N - 1; ++k) {
+      w(U3, k) = w(U3, k + 1);
+      w(PIL3, k) = w(PIL3, k + 1);
+      w(PIU3, k) = w(PIU3, k + 1);
+      for (int q = 0; q < 3; ++q) {
+        w(X3 + q, k + 1) = w(X3 + q, k + 2);
+        w(LAM3 + q, k) = w(LAM3 + q, k + 1);
+      }
+    }
+    plant_interval<double>(m, tp, j, i, F, n);
+    F_prev = F;
+  }
+  out.phi = phi / (double)(K + 1);
+  return out;
+}
+
+}  // namespace mc

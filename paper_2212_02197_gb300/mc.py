@@ -52,7 +52,8 @@ class McController(C.Structure):
                 ("ls_max", C.c_int32), ("sqp_tol", C.c_double), ("qp_solver", C.c_int32),
                 ("ip_max_it", C.c_int32), ("ip_tol", C.c_double), ("u_scale", C.c_double),
                 ("x_scale", C.c_double), ("N_min", C.c_int32), ("sqp_max_it_min", C.c_int32),
-                ("schedule", C.c_int32), ("threads_per_sm", C.c_int32)]
+                ("schedule", C.c_int32), ("threads_per_sm", C.c_int32),
+                ("nx_model", C.c_int32)]
 
 
 class McStats(C.Structure):
@@ -178,6 +179,7 @@ def make_ctrl(cd: dict) -> McController:
     c.sqp_max_it_min = int(cd.get("sqp_max_it_min", 0))
     c.schedule = SCHEDULES[cd.get("schedule", "static")]
     c.threads_per_sm = int(cd.get("threads_per_sm", 0))
+    c.nx_model = int(cd.get("nx_model", 1))
     return c
 
 

@@ -81,3 +81,39 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(mc._build, "LIB", "/nonexistent/libmc_gb300.so")
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mc.lib()
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every field of the Python mirrors sits at the offset the C compiler
+    gives it in include/mc.h, and the struct sizes agree."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2212_02197_gb300 import mc
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    header = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                          "include", "mc.h")
+    structs = {"mc_model_t": mc.McModel, "mc_controller_t": mc.McController,
+               "mc_stats_t": mc.McStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{header}"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        cname, field, value = line.split()
+        py = structs[cname]
+        if field == "size":
+            assert ctypes.sizeof(py) == int(value), cname
+        else:
+            assert getattr(py, field).offset == int(value), (cname, field)

@@ -1,0 +1,77 @@
+"""The three-state NMPC (3x3 CD-EKF, three states per OCP stage, Riccati
+QP with a 3x3 Riccati matrix) on the GPU against the oracle's three-state
+NMPC (condensed dense QP)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_02197_gb300 import mc, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+WL = "cstr_30k_x240_N20_fp64_nx3"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2212_02197_gb300 import _build
+
+    _build.build()
+    oracle.build()
+
+
+def _run(m, c, n, seed):
+    h = mc.MonteCarlo(m, c, n, seed)
+    h.run()
+    st = h.stats(timeout_ms=600000)
+    phi, cnt = h.phi(), h.counters()
+    h.close()
+    return phi, cnt, st
+
+
+def test_first_ocp_matches_oracle():
+    """One control step: Phi depends on the first OCP's input only, and the
+    SQP iteration counts of that OCP are compared too."""
+    w = W.get(WL)
+    m = dict(w["model"], n_steps=1)
+    n = 200
+    phi, cnt, _ = _run(m, w["nmpc"], n, w["seed"])
+    ref = oracle.run(m, w["nmpc"], w["seed"], 0, n)
+    np.testing.assert_allclose(phi, ref["phi"], rtol=1e-9, atol=0)
+    assert np.mean(np.abs(cnt["sqp_iters"] - ref["sqp_iters"]) <= 1) >= 0.95
+
+
+def test_closed_loop_matches_oracle():
+    """160 trajectories (5 warps), 60 steps, with the T_in step: per-trajectory
+    relative Phi within 1e-6 except where an OCP hit the iteration limit."""
+    w = W.get(WL)
+    m = dict(w["model"], n_steps=60)
+    n = 160
+    phi, cnt, st = _run(m, w["nmpc"], n, w["seed"])
+    ref = oracle.run(m, w["nmpc"], w["seed"], 0, n)
+    rel = np.abs(phi - ref["phi"]) / np.abs(ref["phi"])
+    hit = (ref["n_ocp_failed"] > 0) | (cnt["n_ocp_failed"] > 0)
+    assert np.all(rel[~hit] <= 1e-6), (rel[~hit].max(), np.argmax(np.where(hit, 0, rel)))
+    assert np.all(rel[hit] <= 1e-3)
+    assert st["n_ocp"] == n * 60 and st["n_nonfinite"] == 0
+    # the total SQP effort agrees closely
+    assert abs(cnt["sqp_iters"].sum() / ref["sqp_iters"].sum() - 1.0) < 0.02
+
+
+def test_three_state_and_one_state_controllers_agree_roughly():
+    """Both control the same plant; with the plant near the reaction-invariant
+    manifold they track alike (mean Phi within 5 %)."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=60)
+    phi3, _, _ = _run(m, dict(w["nmpc"], nx_model=3, schedule="static"), 96, w["seed"])
+    phi1, _, _ = _run(m, w["nmpc"], 96, w["seed"])
+    assert abs(phi3.mean() / phi1.mean() - 1.0) < 0.05
+
+
+def test_three_state_validation():
+    w = W.get(WL)
+    base = w["nmpc"]
+    for bad in (dict(precision="mixed"), dict(schedule="persistent"), dict(qp_solver="ipm"),
+                dict(nx_model=2)):
+        with pytest.raises(mc.McError):
+            mc.MonteCarlo(w["model"], dict(base, **bad), 4, w["seed"])
