@@ -258,6 +258,46 @@ def test_paper_scale_sampled_parity():
             assert st["n_ocp_failed"] <= 1e-3 * st["n_ocp"]
 
 
+def test_uneven_study_full_size_sampled():
+    """The 262,144-trajectory uneven study (horizons 10..40, SQP limits 5..30,
+    120 steps) in one launch of the persistent schedule; three blocks of 16
+    trajectories (start, middle, end of the index range) against the oracle."""
+    w = W.get("cstr_262k_x120_N10to40_uneven")
+    n = w["n_traj"]
+    h = mc.MonteCarlo(w["model"], w["nmpc"], n, w["seed"])
+    h.run()
+    st = h.stats(timeout_ms=1800000)
+    phi, cnt = h.phi(), h.counters()
+    h.close()
+    assert st["n_traj"] == n and st["n_nonfinite"] == 0
+    assert st["n_ocp"] == n * w["model"]["n_steps"]
+    for j0 in (0, n // 2 - 8, n - 16):
+        ref = oracle.run(w["model"], w["nmpc"], w["seed"], j0, j0 + 16)
+        compare_phi(phi[j0:j0 + 16], ref, {k: v[j0:j0 + 16] for k, v in cnt.items()}, 1e-6)
+
+
+def test_mixed_100k_study_full_size_sampled():
+    """The 100,000-trajectory mixed-precision study (N = 30, E_a/R lognormal)
+    in one launch; blocks of trajectories across the range against the FP64
+    oracle: mixed precision moves Phi by ~1e-4 relative (median)."""
+    w = W.get("cstr_100k_x240_N30_mixed")
+    n = w["n_traj"]
+    h = mc.MonteCarlo(w["model"], w["nmpc"], n, w["seed"])
+    h.run()
+    st = h.stats(timeout_ms=1800000)
+    phi = h.phi()
+    h.close()
+    assert st["n_traj"] == n and st["n_nonfinite"] == 0
+    assert st["n_ocp"] == n * w["model"]["n_steps"]
+    rels = []
+    c64 = dict(w["nmpc"], precision="fp64", sqp_tol=1e-5, ls_max=30)
+    for j0 in (0, n // 2 - 12, n - 24):
+        ref = oracle.run(w["model"], c64, w["seed"], j0, j0 + 24)["phi"]
+        rels.append(np.abs(phi[j0:j0 + 24] - ref) / np.abs(ref))
+    rel = np.concatenate(rels)
+    assert np.median(rel) < 1e-3 and np.max(rel) < 5e-2
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_range_split_is_bit_identical():
