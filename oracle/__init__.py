@@ -61,7 +61,8 @@ class Ctrl(C.Structure):
                 ("u_min", C.c_double), ("u_max", C.c_double), ("kP", C.c_double),
                 ("kI", C.c_double), ("kaw", C.c_double), ("Qz", C.c_double),
                 ("P0", C.c_double), ("sqp_tol", C.c_double), ("u_scale", C.c_double),
-                ("x_scale", C.c_double), ("N_min", C.c_int32), ("it_min", C.c_int32)]
+                ("x_scale", C.c_double), ("N_min", C.c_int32), ("it_min", C.c_int32),
+                ("Ru", C.c_double), ("Qn", C.c_double)]
 
 
 class TrajOut(C.Structure):
@@ -140,6 +141,9 @@ def lib():
             L.or_sqp3.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_double, _dp, _dp, _dp,
                                   _dp, _dp, _dp, _dp, C.POINTER(SqpInfo)]
             L.or_sqp3.restype = C.c_int
+            L.or_ocp_sens.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_double, C.c_double,
+                                      _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.or_ocp_sens.restype = C.c_int
             L.or_pi_phi_cs.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64,
                                        C.c_int64, C.c_int, C.c_double, _dp]
             L.or_pi_phi_cs.restype = C.c_double
@@ -181,6 +185,8 @@ def make_ctrl(cd: dict) -> Ctrl:
               "x_scale"):
         setattr(c, k, float(cd[k]))
     c.nx_model = int(cd.get("nx_model", 1))
+    c.Ru = float(cd.get("Ru", 0.0))
+    c.Qn = float(cd.get("Qn", 0.0))
     c.N_min = int(cd.get("N_min", 0))
     c.it_min = int(cd.get("sqp_max_it_min", 0))
     assert 1 <= c.N <= MAX_N
@@ -473,3 +479,13 @@ def sqp3(model: dict, ctrl: dict, EaR: float, x0, zbar, u, x, lam=None, pil=None
               _p(piu), C.byref(info))
     d = {f: getattr(info, f) for f, _ in SqpInfo._fields_ if f != "pad0"}
     return u, x.reshape(N + 1, 3), lam.reshape(N, 3), pil, piu, d
+
+
+def ocp_sens(model: dict, ctrl: dict, EaR: float, x0: float, zbar, u, x, lam, pil, piu):
+    """du_0/d(x_0, Q_z, R_u, Q_n) at an OCP solution (implicit differentiation)."""
+    L = lib()
+    m, c = make_model(model), make_ctrl(ctrl)
+    arrs = [_arr(a).copy() for a in (zbar, u, x, lam, pil, piu)]
+    out = np.zeros(4)
+    st = L.or_ocp_sens(C.byref(m), C.byref(c), EaR, x0, *[_p(a) for a in arrs], _p(out))
+    return st, out

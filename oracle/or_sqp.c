@@ -214,11 +214,14 @@ typedef struct {
   double f;
 } eval_t;
 
-/* Objective of Sec. VII-A, phi = sum_{k=1..N} Q_z (z_k - zbar_k)^2 T_s, its
- * gradient, and the shooting constraints g_k = F_k - x_{k+1} with the
- * sensitivities A_k, B_k of F_k.  The NLP variables are scaled: the OCP state
- * is x = n_T / x_scale (so z = x x_scale / V) and the OCP input is v, with
- * flow F = v Fconv in L/s. */
+/* Objective of Sec. VII-A, phi = sum_{k=1..N} Q_z (z_k - zbar_k)^2 T_s, with
+ * the optional weights of the extended objective
+ *   + sum_{k=1..N} R_u (v_{k-1} - vbar_k)^2 T_s + Q_n (z_N - zbar_N)^2,
+ * vbar_k the steady-state input F_ss(zbar_k) in OCP units (both weights are
+ * 0 in the paper's objective); its gradient; and the shooting constraints
+ * g_k = F_k - x_{k+1} with the sensitivities A_k, B_k of F_k.  The NLP
+ * variables are scaled: the OCP state is x = n_T / x_scale (so
+ * z = x x_scale / V) and the OCP input is v, with flow F = v Fconv in L/s. */
 static void evaluate(const or_model* m, const or_ctrl* c, double EaR, double Fconv,
                      double x0, const double* zbar, const double* u, const double* x,
                      eval_t* e) {
@@ -240,6 +243,18 @@ static void evaluate(const or_model* m, const or_ctrl* c, double EaR, double Fco
     const double dz = x[k] * xs / m->V - zbar[k];
     f += c->Qz * dz * dz * m->Ts;
     e->q[k] = 2.0 * c->Qz * dz * m->Ts * xs / m->V;
+  }
+  if (c->Ru != 0.0) {
+    for (int k = 0; k < N; ++k) {
+      const double dv = u[k] - or_Fss(m, EaR, zbar[k + 1]) / Fconv;
+      f += c->Ru * dv * dv * m->Ts;
+      e->r[k] = 2.0 * c->Ru * dv * m->Ts;
+    }
+  }
+  if (c->Qn != 0.0) {
+    const double dz = x[N] * xs / m->V - zbar[N];
+    f += c->Qn * dz * dz;
+    e->q[N] += 2.0 * c->Qn * dz * xs / m->V;
   }
   e->f = f;
 }
@@ -445,4 +460,138 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
   }
   info->iters = nqp;
   return info->status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sensitivity of the OCP solution's first input u_0 to the initial state x_0
+ * (scaled) and to the objective weights (Q_z, R_u, Q_n), by implicit
+ * differentiation of the KKT conditions at a solution (u, x, lam, pil, piu)
+ * of or_sqp: the tangent (dx, du) solves the equality-constrained QP whose
+ * Hessian is that of the Lagrangian, whose linear term is the derivative of
+ * the Lagrangian gradient with respect to the parameter, and whose
+ * constraints are the linearised dynamics (dx_1 = A_0 dx_0 + B_0 du_0) with
+ * the active bounds held (du_k = 0).  The second derivatives of the shooting
+ * map come from central differences of its analytic first derivatives; the
+ * QP is solved through its full KKT matrix by Gaussian elimination with
+ * partial pivoting.  A bound is active when u_k lies on it and its
+ * multiplier exceeds 1e-10.  out[0..3] = du_0/dx_0, du_0/dQ_z, du_0/dR_u,
+ * du_0/dQ_n; returns 0, or -1 if the KKT matrix is singular. */
+
+static int dense_solve(int n, double* a, double* b) {
+  for (int j = 0; j < n; ++j) {
+    int piv = j;
+    for (int i = j + 1; i < n; ++i)
+      if (fabs(a[i * n + j]) > fabs(a[piv * n + j])) piv = i;
+    if (!(fabs(a[piv * n + j]) > 0.0)) return -1;
+    if (piv != j) {
+      for (int k = 0; k < n; ++k) {
+        const double t = a[j * n + k];
+        a[j * n + k] = a[piv * n + k];
+        a[piv * n + k] = t;
+      }
+      const double t = b[j];
+      b[j] = b[piv];
+      b[piv] = t;
+    }
+    for (int i = j + 1; i < n; ++i) {
+      const double f = a[i * n + j] / a[j * n + j];
+      if (f == 0.0) continue;
+      for (int k = j; k < n; ++k) a[i * n + k] -= f * a[j * n + k];
+      b[i] -= f * b[j];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int k = i + 1; k < n; ++k) s -= a[i * n + k] * b[k];
+    b[i] = s / a[i * n + i];
+  }
+  return 0;
+}
+
+int or_ocp_sens(const or_model* m, const or_ctrl* c, double EaR, double x0, const double* zbar,
+                const double* u, const double* x, const double* lam, const double* pil,
+                const double* piu, double* out) {
+  const int N = c->N;
+  const double xs = c->x_scale, Ts = m->Ts;
+  const double Fconv = c->u_scale / 60000.0;
+  const double umin = c->u_min / c->u_scale, umax = c->u_max / c->u_scale;
+  const double sz = xs / m->V;                       /* dz/dx */
+  static __thread double Fxx[OR_MAX_N], Fxu[OR_MAX_N], Fuu[OR_MAX_N], Ak[OR_MAX_N], Bk[OR_MAX_N];
+  int act[OR_MAX_N];
+  for (int k = 0; k < N; ++k) {
+    const double xk = (k == 0) ? x0 : x[k];
+    double Fn, a, b, ap, bp, am, bm;
+    or_rk4_interval(m, EaR, c->n_rk4, Ts, xk * xs, u[k], Fconv, &Fn, &a, &b);
+    Ak[k] = a;
+    Bk[k] = b / xs;
+    /* second derivatives of the scaled map F(x, v) = F_n(x xs, v) / xs */
+    const double hx = 1e-5 * fabs(xk), hv = 1e-5;
+    or_rk4_interval(m, EaR, c->n_rk4, Ts, (xk + hx) * xs, u[k], Fconv, &Fn, &ap, &bp);
+    or_rk4_interval(m, EaR, c->n_rk4, Ts, (xk - hx) * xs, u[k], Fconv, &Fn, &am, &bm);
+    Fxx[k] = (ap - am) / (2.0 * hx);
+    Fxu[k] = (bp - bm) / (2.0 * hx) / xs;
+    or_rk4_interval(m, EaR, c->n_rk4, Ts, xk * xs, u[k] + hv, Fconv, &Fn, &ap, &bp);
+    or_rk4_interval(m, EaR, c->n_rk4, Ts, xk * xs, u[k] - hv, Fconv, &Fn, &am, &bm);
+    Fuu[k] = (bp - bm) / (2.0 * hv) / xs;
+    act[k] = ((u[k] - umin <= 1e-12 && pil[k] > 1e-10) || (umax - u[k] <= 1e-12 && piu[k] > 1e-10));
+  }
+  /* unknowns: du_0..du_{N-1}, dx_1..dx_N, then multipliers of the N dynamics
+   * rows and of the active bounds */
+  int na = 0;
+  for (int k = 0; k < N; ++k) na += act[k];
+  const int nv = 2 * N, n = nv + N + na;
+  static __thread double K[(4 * OR_MAX_N) * (4 * OR_MAX_N)], rhs[4 * OR_MAX_N];
+#define IU(k) (k)
+#define IX(k) (N + (k) - 1)
+  for (int dir = 0; dir < 4; ++dir) {
+    for (int i = 0; i < n * n; ++i) K[i] = 0.0;
+    for (int i = 0; i < n; ++i) rhs[i] = 0.0;
+    const double dx0 = (dir == 0) ? 1.0 : 0.0;
+    const double dQz = (dir == 1), dRu = (dir == 2), dQn = (dir == 3);
+    /* Hessian of the Lagrangian and the linear terms */
+    for (int k = 0; k < N; ++k) {
+      K[IU(k) * n + IU(k)] += 2.0 * Ts * c->Ru - lam[k] * Fuu[k];
+      if (k >= 1) {
+        K[IX(k) * n + IX(k)] += 2.0 * Ts * c->Qz * sz * sz - lam[k] * Fxx[k];
+        K[IX(k) * n + IU(k)] += -lam[k] * Fxu[k];
+        K[IU(k) * n + IX(k)] += -lam[k] * Fxu[k];
+      } else {
+        rhs[IU(0)] -= -lam[0] * Fxu[0] * dx0;              /* x_0 cross term */
+      }
+      const double vb = or_Fss(m, EaR, zbar[k + 1]) / Fconv;
+      rhs[IU(k)] -= 2.0 * Ts * dRu * (u[k] - vb);
+    }
+    K[IX(N) * n + IX(N)] += (2.0 * Ts * c->Qz + 2.0 * c->Qn) * sz * sz;
+    for (int k = 1; k <= N; ++k) {
+      const double dz = x[k] * sz - zbar[k];
+      rhs[IX(k)] -= 2.0 * Ts * dQz * dz * sz;
+      if (k == N) rhs[IX(k)] -= 2.0 * dQn * dz * sz;
+    }
+    /* dynamics rows: dx_{k+1} - A_k dx_k - B_k du_k = (k == 0 ? A_0 dx_0 : 0) */
+    for (int k = 0; k < N; ++k) {
+      const int row = nv + k;
+      K[row * n + IX(k + 1)] = 1.0;
+      K[IX(k + 1) * n + row] = 1.0;
+      K[row * n + IU(k)] = -Bk[k];
+      K[IU(k) * n + row] = -Bk[k];
+      if (k >= 1) {
+        K[row * n + IX(k)] = -Ak[k];
+        K[IX(k) * n + row] = -Ak[k];
+      }
+      rhs[row] = (k == 0) ? Ak[0] * dx0 : 0.0;
+    }
+    int r = nv + N;
+    for (int k = 0; k < N; ++k)
+      if (act[k]) {
+        K[r * n + IU(k)] = 1.0;
+        K[IU(k) * n + r] = 1.0;
+        rhs[r] = 0.0;
+        ++r;
+      }
+    if (dense_solve(n, K, rhs) != 0) return -1;
+    out[dir] = rhs[IU(0)];
+  }
+#undef IU
+#undef IX
+  return 0;
 }

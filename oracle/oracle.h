@@ -74,6 +74,8 @@ typedef struct {
   double x_scale;       /* unit of the OCP state variable, in K L            */
   int32_t N_min;        /* > 0: per-trajectory horizon uniform on N_min..N   */
   int32_t it_min;       /* > 0: per-trajectory SQP limit on it_min..max_it   */
+  double Ru;            /* input-deviation weight of the NMPC objective      */
+  double Qn;            /* terminal output weight of the NMPC objective      */
 } or_ctrl;
 
 /* Per-trajectory result of one closed-loop simulation. */
@@ -151,6 +153,12 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
 /* ---- PI controller, Eq. (PI) ---- */
 double or_pi_step(const or_ctrl* c, double Ts, double ybar, double y, double ubar,
                   double* Ihat);
+
+/* du_0/d(x_0, Q_z, R_u, Q_n) at an OCP solution of or_sqp (implicit
+ * differentiation of its KKT conditions); 0 or -1 (singular KKT matrix). */
+int or_ocp_sens(const or_model* m, const or_ctrl* c, double EaR, double x0, const double* zbar,
+                const double* u, const double* x, const double* lam, const double* pil,
+                const double* piu, double* out);
 
 /* ---- closed loop and Monte Carlo driver ---- */
 /* trace (optional, may be NULL): per step i = 0..K-1 the row

@@ -78,7 +78,7 @@ def nmpc(N: int = 20, u_max: float = 800.0, precision: str = "fp64") -> dict:
     mixed = precision == "mixed"
     return dict(kind="nmpc", precision=precision, N=int(N), n_rk4=5, sqp_max_it=100,
                 ls_max=3 if mixed else 30, u_min=0.0, u_max=float(u_max), kP=-1e-3, kI=-1e-4,
-                kaw=-1e-1, Qz=1.0, P0=1e-6, sqp_tol=1e-3 if mixed else 1e-5,
+                kaw=-1e-1, Qz=1.0, Ru=0.0, Qn=0.0, P0=1e-6, sqp_tol=1e-3 if mixed else 1e-5,
                 u_scale=float(u_max), x_scale=CSTR["V"], qp_solver="active_set", ip_max_it=60,
                 ip_tol=1e-14, schedule="static" if mixed else "persistent")
 

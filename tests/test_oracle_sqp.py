@@ -149,3 +149,115 @@ def test_sqp_matches_grid_search_on_horizon_two(x0, z1, z2):
     assert info["status"] == 0
     fsqp = objective(c, shoot(c, x0, u), zb)
     assert fsqp <= fbest + 1e-9 * max(1.0, abs(fbest))
+
+
+# ------------------------------------------------------------------ weighted objective
+
+def weighted_objective(c, x, u, zb):
+    """Extended objective: the paper's output term plus R_u (v_{k-1} - vbar_k)^2 T_s
+    and Q_n (z_N - zbar_N)^2, vbar_k the steady-state input of zbar_k."""
+    Fconv = c["u_scale"] / 60000.0
+    z = x * c["x_scale"] / V
+    f = np.sum(c["Qz"] * (z[1:] - zb[1:]) ** 2 * M["Ts"])
+    vbar = np.array([oracle.Fss(M, zk) / Fconv for zk in zb[1:]])
+    f += np.sum(c["Ru"] * (np.asarray(u) - vbar) ** 2 * M["Ts"])
+    f += c["Qn"] * (z[-1] - zb[-1]) ** 2
+    return float(f)
+
+
+@pytest.mark.parametrize("Ru,Qn", [(0.5, 0.0), (0.0, 4.0), (2.0, 1.0)])
+def test_weighted_objective_matches_grid_search_on_horizon_two(Ru, Qn):
+    from scipy.optimize import minimize
+
+    c = dict(ctrl(2, 1e-8), Ru=Ru, Qn=Qn)
+    x0 = 300.0
+    zb = np.array([0.0, 305.0, 310.0])
+
+    def fobj(uv):
+        return weighted_objective(c, shoot(c, x0, uv), uv, zb)
+
+    g = np.linspace(0.0, 1.0, 101)
+    vals = np.array([[fobj((a, b)) for b in g] for a in g])
+    fbest = np.inf
+    for idx in np.argsort(vals.ravel())[:5]:
+        a, b = g[idx // 101], g[idx % 101]
+        r = minimize(fobj, [a, b], bounds=[(0, 1), (0, 1)], method="L-BFGS-B",
+                     options=dict(ftol=1e-15, gtol=1e-12))
+        fbest = min(fbest, r.fun, vals.ravel()[idx])
+    u, x, lam, pil, piu, info = oracle.sqp(M, c, M["EaR"], x0, zb, [0.5, 0.5], [x0] * 3)
+    assert info["status"] == 0 and info["kkt_grad"] <= 1e-8
+    assert fobj(u) <= fbest + 1e-9 * max(1.0, abs(fbest))
+    assert info["f"] == pytest.approx(fobj(u), rel=1e-9)
+
+
+def test_large_input_weight_drives_the_inputs_to_the_steady_state():
+    """Q_z = 0 and R_u dominant: the minimiser is the reference input vbar_k
+    itself (clipped into the bounds), whatever the set-points ask of z."""
+    N = 6
+    c = dict(ctrl(N, 1e-10), Qz=0.0, Ru=1.0, Qn=0.0)
+    x0 = 300.0
+    zb = np.array([0.0, 282.0, 282.0, 290.0, 290.0, 300.0, 300.0])
+    u, x, lam, pil, piu, info = oracle.sqp(M, c, M["EaR"], x0, zb, np.full(N, 0.5),
+                                           np.full(N + 1, x0))
+    assert info["status"] == 0
+    Fconv = c["u_scale"] / 60000.0
+    vbar = np.clip([oracle.Fss(M, z) / Fconv for z in zb[1:]], 0.0, 1.0)
+    np.testing.assert_allclose(u, vbar, rtol=0, atol=1e-8)
+
+
+# ------------------------------------------------------------------ OCP sensitivity
+
+def _solve(c, x0, zb, N, converged=True):
+    u, x, lam, pil, piu, info = oracle.sqp(M, c, M["EaR"], x0, zb, np.full(N, 0.5),
+                                           np.full(N + 1, x0))
+    # near 1e-8 the merit's rounding floor can stop a solve at the iteration
+    # limit with its input already accurate; only the base point must converge
+    if converged:
+        assert info["status"] == 0, info
+    return u, x, lam, pil, piu
+
+
+# cases whose first input is interior (above the set-point the reactor needs
+# flow to cool; below it the input sits on its lower bound)
+INTERIOR = [(290.5, 290.0), (340.5, 340.0)]
+
+
+@pytest.mark.parametrize("x0,zset", INTERIOR)
+def test_ocp_sensitivity_matches_differences_of_the_solution(x0, zset):
+    """du_0/d(x_0, Q_z, R_u, Q_n) from the KKT system against central
+    differences of OCP solutions converged to 1e-9 (the steps are sized to
+    that accuracy)."""
+    N = 8
+    c = dict(ctrl(N, 1e-8), Ru=0.3, Qn=2.0)
+    zb = np.full(N + 1, zset)
+    u, x, lam, pil, piu = _solve(c, x0, zb, N)
+    assert 0.0 < u[0] < 1.0
+    st, s = oracle.ocp_sens(M, c, M["EaR"], x0, zb, u, x, lam, pil, piu)
+    assert st == 0
+    h = 1e-2
+    fd = [(_solve(c, x0 + h, zb, N, False)[0][0] - _solve(c, x0 - h, zb, N, False)[0][0]) / (2 * h)]
+    for key in ("Qz", "Ru", "Qn"):
+        hk = 1e-3 * max(1.0, c[key])
+        up = _solve(dict(c, **{key: c[key] + hk}), x0, zb, N, False)[0][0]
+        dn = _solve(dict(c, **{key: c[key] - hk}), x0, zb, N, False)[0][0]
+        fd.append((up - dn) / (2 * hk))
+    np.testing.assert_allclose(s[0], fd[0], rtol=1e-5)
+    np.testing.assert_allclose(s[1:], fd[1:], rtol=1e-4, atol=1e-7 * abs(fd[0]))
+
+
+def test_ocp_sensitivity_exact_zeros():
+    """With R_u = Q_n = 0 the minimiser does not depend on Q_z (the objective
+    only scales), and an input held on an active bound does not move."""
+    N = 8
+    c = ctrl(N, 1e-8)
+    x0, zs = INTERIOR[0]
+    zb = np.full(N + 1, zs)
+    u, x, lam, pil, piu = _solve(c, x0, zb, N)
+    st, s = oracle.ocp_sens(M, c, M["EaR"], x0, zb, u, x, lam, pil, piu)
+    assert st == 0 and abs(s[0]) > 0.1
+    assert abs(s[1]) <= 1e-7 * abs(s[0])
+    zb2 = np.full(N + 1, 306.0)          # heating: the first input on its lower bound
+    u2, x2, lam2, pil2, piu2 = _solve(c, 300.0, zb2, N)
+    assert u2[0] == 0.0 and pil2[0] > 1e-10
+    st2, s2 = oracle.ocp_sens(M, c, M["EaR"], 300.0, zb2, u2, x2, lam2, pil2, piu2)
+    assert st2 == 0 and np.all(np.abs(s2) <= 1e-12)
