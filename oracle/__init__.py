@@ -144,6 +144,9 @@ def lib():
             L.or_ocp_sens.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_double, C.c_double,
                                       _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             L.or_ocp_sens.restype = C.c_int
+            L.or_nmpc_grad_run.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64,
+                                           C.c_int64, C.c_int64, C.c_int, _dp, _dp,
+                                           C.POINTER(C.c_int)]
             L.or_pi_phi_cs.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_uint64,
                                        C.c_int64, C.c_int, C.c_double, _dp]
             L.or_pi_phi_cs.restype = C.c_double
@@ -489,3 +492,20 @@ def ocp_sens(model: dict, ctrl: dict, EaR: float, x0: float, zbar, u, x, lam, pi
     out = np.zeros(4)
     st = L.or_ocp_sens(C.byref(m), C.byref(c), EaR, x0, *[_p(a) for a in arrs], _p(out))
     return st, out
+
+
+def nmpc_grad(model: dict, ctrl: dict, seed: int, j0: int, j1: int, threads: int | None = None):
+    """Phi_j and dPhi_j/d(Q_z, R_u, Q_n) of NMPC trajectories j0..j1-1 (complex step
+    with implicit OCP derivatives); returns (phi[n], dphi[n, 3], sens_fail[n])."""
+    L = lib()
+    m, c = make_model(model), make_ctrl(dict(ctrl, kind="nmpc"))
+    n = j1 - j0
+    phi = np.zeros(max(n, 1))
+    dphi = np.zeros((max(n, 1), 3))
+    fails = np.zeros(max(n, 1), dtype=np.int32)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    if n > 0:
+        L.or_nmpc_grad_run(C.byref(m), C.byref(c), seed, j0, j1, int(threads), _p(phi),
+                           _p(dphi), fails.ctypes.data_as(C.POINTER(C.c_int)))
+    return phi[:n], dphi[:n], fails[:n]

@@ -194,6 +194,14 @@ double or_pi_phi_cs(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t 
  * host threads (h_cs = 1e-20 |k|). */
 void or_pi_grad_run(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j0,
                     int64_t j1, int n_threads, double* phi, double* dphi);
+/* dPhi_j/d(Q_z, R_u, Q_n) of the one-state NMPC closed loop: complex step
+ * through plant, measurement and CD-EKF, each OCP by its solution map with
+ * the implicit derivative of or_ocp_sens (which = 0 Q_z, 1 R_u, 2 Q_n);
+ * *n_sens_fail counts OCPs whose KKT matrix was singular. */
+double or_nmpc_phi_cs(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j, int which,
+                      double h_cs, double* dphi, int* n_sens_fail);
+void or_nmpc_grad_run(const or_model* m, const or_ctrl* c, uint64_t seed, int64_t j0,
+                      int64_t j1, int n_threads, double* phi, double* dphi, int* fails);
 
 #ifdef __cplusplus
 }

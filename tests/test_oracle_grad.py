@@ -83,3 +83,47 @@ def test_complex_step_is_insensitive_to_its_step(w):
         _, a = oracle.pi_phi_cs(w["model"], c, w["seed"], 5, q, 1e-20 * h)
         _, b = oracle.pi_phi_cs(w["model"], c, w["seed"], 5, q, 1e-30 * h)
         assert a == pytest.approx(b, rel=1e-12)
+
+
+# ------------------------------------------------------------------ NMPC weights
+
+@pytest.fixture(scope="module")
+def wn():
+    oracle.build()
+    w = W.get("cstr_100x120_N20_fp64")
+    return dict(w, model=dict(w["model"], n_steps=12))
+
+
+def test_nmpc_grad_real_part_is_the_simulated_phi(wn):
+    c = dict(wn["nmpc"], Ru=0.2, Qn=1.0)
+    phi, _, fails = oracle.nmpc_grad(wn["model"], c, wn["seed"], 0, 6)
+    ref = oracle.run(wn["model"], c, wn["seed"], 0, 6)["phi"]
+    np.testing.assert_allclose(phi, ref, rtol=1e-12, atol=0)
+    assert np.all(fails == 0)
+
+
+def test_nmpc_grad_matches_central_differences_with_tight_ocps(wn):
+    """With the OCPs solved to 1e-8, the closed loop's Phi is the composition
+    the implicit derivative describes; central differences of the plain
+    oracle (steps 2e-3 of each weight) agree."""
+    c = dict(wn["nmpc"], Ru=0.2, Qn=1.0, sqp_tol=1e-8, sqp_max_it=300)
+    _, d, _ = oracle.nmpc_grad(wn["model"], c, wn["seed"], 0, 6)
+    fd = []
+    for k in ("Qz", "Ru", "Qn"):
+        hk = 2e-3 * c[k]
+        a = oracle.run(wn["model"], dict(c, **{k: c[k] + hk}), wn["seed"], 0, 6)["phi"]
+        b = oracle.run(wn["model"], dict(c, **{k: c[k] - hk}), wn["seed"], 0, 6)["phi"]
+        fd.append((a - b) / (2 * hk))
+    fd = np.array(fd).T
+    scale = np.abs(fd).max(axis=0)
+    assert np.all(np.abs(d - fd) <= 1e-3 * np.abs(fd) + 1e-4 * scale), np.abs(d - fd) / scale
+
+
+def test_nmpc_grad_paper_objective_is_invariant_to_the_output_weight(wn):
+    """R_u = Q_n = 0: every KKT point is invariant to scaling Q_z, so the
+    derivative along Q_z vanishes, while R_u and Q_n still move Phi."""
+    m = dict(wn["model"], n_steps=60)     # past the first set-point change
+    _, d, _ = oracle.nmpc_grad(m, wn["nmpc"], wn["seed"], 0, 6)
+    assert np.abs(d[:, 1]).max() > 0
+    # the OCPs stop at the 1e-5 KKT test, so the invariance holds to that order
+    assert np.all(np.abs(d[:, 0]) <= 1e-4 * np.abs(d[:, 1:]).max())
