@@ -420,6 +420,75 @@ def main():
                 "fd_grad_mean": fd,
                 "fd_rel_err": [abs(f / g - 1.0) if g != 0 else None for f, g in zip(fd, gm)]}
 
+    # gradient of mean Phi of the NMPC study with respect to the objective
+    # weights (Q_z, R_u, Q_n) at R_u = 0.2, Q_n = 1.0 (with the paper's
+    # objective, R_u = Q_n = 0, the Q_z direction vanishes): implicit
+    # derivatives of the OCPs' KKT points, forward-mode tangents of plant and
+    # CD-EKF, static schedule.  Checked by central differences where that is
+    # meaningful: OCPs solved to 1e-7 (a looser SQP lags the exact solution
+    # map), steps 1e-2 of each weight, 2,000 trajectories x 24 samples, over
+    # the trajectories whose OCPs all converged.
+    ngrad = None
+    if (not args.no_grad and w["nmpc"]["precision"] == "fp64" and
+            w["nmpc"].get("nx_model", 1) != 3):
+        cw = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+        hg = mc.MonteCarlo(dict(w["model"], n_steps=min(24, w["model"]["n_steps"])), cw, j1,
+                           w["seed"])
+        for _ in range(max(1, args.warmup)):
+            hg.nmpc_grad(stream, j0, j1)
+        hg.sync()
+        hg.close()
+        hg = mc.MonteCarlo(w["model"], cw, j1, w["seed"])
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        flush.zero_()
+        a_ev.record(stream)
+        hg.nmpc_grad(stream, j0, j1)
+        b_ev.record(stream)
+        barrier()
+        ng_ms = a_ev.elapsed_time(b_ev)
+        ng_mean = hg.grad_mean()
+        ng_st = hg.stats()
+        hg.close()
+        nf = min(2000, T)
+        cf = dict(cw, sqp_tol=1e-7, sqp_max_it=300)
+        hf = mc.MonteCarlo(dict(w["model"], n_steps=min(24, w["model"]["n_steps"])), cf, nf,
+                           w["seed"])
+        hf.nmpc_grad(stream)
+        hf.sync()
+        gf = hf.grad()
+        okf = hf.counters()["n_ocp_failed"] == 0
+        fdr = {}
+        for kk in ("Qz", "Ru", "Qn"):
+            hk = 1e-2 * cf[kk]
+            for sgn in (1, -1):
+                ww = {q: cf[q] for q in ("Qz", "Ru", "Qn")}
+                ww[kk] += sgn * hk
+                hf.set_nmpc_weights(ww["Qz"], ww["Ru"], ww["Qn"])
+                hf.run(stream)
+                hf.sync()
+                fdr[(kk, sgn)] = hf.phi()
+                okf &= hf.counters()["n_ocp_failed"] == 0
+        hf.close()
+        fd_err = []
+        for q, kk in enumerate(("Qz", "Ru", "Qn")):
+            hk = 1e-2 * cf[kk]
+            fdm = float(((fdr[(kk, 1)] - fdr[(kk, -1)])[okf] / (2 * hk)).mean())
+            tgm = float(gf[okf, q].mean())
+            fd_err.append(abs(fdm / tgm - 1.0) if tgm != 0 else None)
+        if world > 1:
+            t = torch.tensor([ng_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ng_ms = float(t.item())
+        ngrad = {"what": "d mean Phi / d(Q_z, R_u, Q_n) of the NMPC study (R_u = 0.2, "
+                         "Q_n = 1), implicit OCP derivatives + forward-mode tangents",
+                 "value": world * T / (ng_ms / 1e3), "unit": "trajectories/s (with tangents)",
+                 "ms_per_step": ng_ms, "phi_mean": ng_st["phi_mean"],
+                 "grad_mean": ng_mean.tolist(),
+                 "ocps_without_sensitivity": ng_st["qp_fail"],
+                 "fd_check": {"trajectories": int(okf.sum()), "of": nf, "n_steps": 24,
+                              "sqp_tol": 1e-7, "h_rel": 1e-2, "rel_err": fd_err}}
+
     # end to end through the C ABI with host buffers: create (config h2d),
     # run, stats and Phi copied back to host, destroy
     e2e_ms = []
@@ -481,6 +550,8 @@ def main():
             line["mixed"] = mixed
         if grad is not None:
             line["pi_grad"] = grad
+        if ngrad is not None:
+            line["nmpc_grad"] = ngrad
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

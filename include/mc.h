@@ -120,6 +120,12 @@ typedef struct {
                              (the paper's); 3 = the three-state model of
                              Eq. (CSTR) with a 3x3 CD-EKF (FP64, active-set
                              QP, static schedule)                             */
+  /* extended NMPC objective (the paper's has both 0):
+   *   + sum_{k=1..N} Ru (v_{k-1} - vbar_k)^2 T_s + Qn (z_N - zbar_N)^2,
+   * v the OCP input (flow / u_scale), vbar_k the steady-state input of the
+   * set-point zbar_k; one-state model only                                  */
+  double Ru;
+  double Qn;
 } mc_controller_t;
 
 typedef enum {
@@ -251,14 +257,36 @@ mc_status mc_set_pi_gains(mc_handle* h, double kP, double kI, double kaw);
 mc_status mc_pi_grad(mc_handle* h, int64_t j0, int64_t j1, int32_t checkpoint_every,
                      void* cuda_stream);
 
-/* Wait for the last mc_pi_grad (as mc_stats does) and write the mean of
- * dPhi_j/d(k_P, k_I, k_aw) over its trajectories with a finite Phi_j to out
- * (3 doubles, host).  MC_ENOTRUN before any mc_pi_grad; MC_WARN_NONFINITE
- * (out still written) when some trajectory was non-finite. */
+/* Replace the objective weights (Q_z, R_u, Q_n) of an NMPC handle.  MC_EINVAL
+ * for a PI handle, negative or non-finite weights, or R_u, Q_n != 0 on the
+ * three-state model. */
+mc_status mc_set_nmpc_weights(mc_handle* h, double Qz, double Ru, double Qn);
+
+/* Run trajectories j0 .. j1-1 of an NMPC handle (one-state model, FP64) and
+ * the tangents of Phi_j with respect to the weights (Q_z, R_u, Q_n) of the
+ * extended objective (mc_controller_t.Ru, .Qn; the paper's has both 0), on
+ * cuda_stream, asynchronously.  Every OCP enters through its solution map
+ * u_0(x-hat, theta) at the KKT point the SQP returns, differentiated
+ * implicitly (Lagrangian Hessian from second-order shooting sensitivities,
+ * active bounds held); the plant, the measurement and the CD-EKF are
+ * differentiated exactly (forward mode).  The warm start does not enter.
+ * Writes Phi_j, the counters (counter 7 also counts OCPs whose reduced
+ * Hessian was not positive definite; their input tangent is 0) and
+ * dPhi_j/d(Q_z, R_u, Q_n) per trajectory (read with mc_grad_mean,
+ * mc_copy_grad).  Static schedule.  MC_EINVAL for a PI, mixed-precision or
+ * three-state handle or a bad range; MC_ENOMEM if the gradient buffers
+ * cannot be had. */
+mc_status mc_nmpc_grad(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream);
+
+/* Wait for the last mc_pi_grad or mc_nmpc_grad (as mc_stats does) and write
+ * the mean of the three derivatives over its trajectories with a finite
+ * Phi_j to out (3 doubles, host).  MC_ENOTRUN before any gradient run;
+ * MC_WARN_NONFINITE (out still written) when some trajectory was non-finite. */
 mc_status mc_grad_mean(mc_handle* h, double out[3], int64_t timeout_ms);
 
-/* Copy dPhi_j/d(k_P, k_I, k_aw) of trajectories j0 .. j0+n-1, row-major
- * n x 3 doubles (NaN rows for non-finite trajectories). */
+/* Copy the per-trajectory derivatives of the last gradient run of
+ * trajectories j0 .. j0+n-1, row-major n x 3 doubles (NaN rows for
+ * non-finite trajectories). */
 mc_status mc_copy_grad(mc_handle* h, int64_t j0, int64_t n, double* dst, int dst_is_device);
 
 /* ---------------------------------------------------------------------------
@@ -309,6 +337,18 @@ mc_status mc_ocp_solve_batch(const mc_model_t* model, const mc_controller_t* ctr
                              int64_t n, const double* x0, const double* EaR,
                              const double* zbar, double* u, double* x, double* lam,
                              double* pil, double* piu, int32_t* info, double* kkt);
+
+/* Sensitivity of n OCP solutions (as mc_ocp_solve_batch returns them): the
+ * derivatives of the first input u_0 with respect to the initial state x_0
+ * (OCP units) and the weights (Q_z, R_u, Q_n), by implicit differentiation of
+ * the KKT conditions (one-state model).  x0, EaR (n); zbar, x (n x (N+1));
+ * u, lam, pil, piu (n x N); sens (n x 4) out; status (n) out: 0, or 1 when
+ * the reduced Hessian is not positive definite (sens 0). */
+mc_status mc_ocp_sens_batch(const mc_model_t* model, const mc_controller_t* ctrl, int64_t n,
+                            const double* x0, const double* EaR, const double* zbar,
+                            const double* u, const double* x, const double* lam,
+                            const double* pil, const double* piu, double* sens,
+                            int32_t* status);
 
 /* ---------------------------------------------------------------------------
  * Statistics without allocation.  The paper has no counterpart to this call;

@@ -24,6 +24,7 @@
 #include "mc_grad.cuh"
 #include "mc_qp_par.cuh"
 #include "mc_nmpc3.cuh"
+#include "mc_grad_nmpc.cuh"
 
 namespace mc {
 
@@ -42,6 +43,27 @@ __global__ void __launch_bounds__(32) k_nmpc(DevModel m, DevCtrl c, int64_t j0, 
     phi[j] = o.phi;
 #pragma unroll
     for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
+  }
+}
+
+// The NMPC closed loop with the tangents of Phi_j in the weights (Q_z, R_u,
+// Q_n) (FP64, static schedule); dphi is n_sims x 3.
+__global__ void __launch_bounds__(32) k_nmpc_grad(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
+                                                  double* __restrict__ phi,
+                                                  int32_t* __restrict__ cnt,
+                                                  double* __restrict__ dphi, double* ws,
+                                                  int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ld) return;
+  const Ws w{ws + t, ld, c.N + 1};
+  for (int64_t j = j0 + t; j < j1; j += ld) {
+    double g[3];
+    const TrajOut o = traj_nmpc_grad(m, c, (uint32_t)j, w, g);
+    phi[j] = o.phi;
+#pragma unroll
+    for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dphi[j * 3 + q] = g[q];
   }
 }
 
@@ -361,6 +383,7 @@ __global__ void k_ocp_batch(DevModel m, DevCtrl c, int64_t n, OcpBatch d, double
   for (int k = 0; k <= N; ++k) {
     w(X, k) = d.x[o2 + k];
     w(ZB, k) = d.zbar[o2 + k];
+    if (c.Ru != 0.0 && k >= 1) w(VB, k) = Fss(m, d.EaR[t], w(ZB, k)) / c.Fconv;
   }
   const SqpInfo si = (c.precision == MC_MIXED) ? sqp_solve<float>(m, c, d.EaR[t], d.x0[t], w)
                                                : sqp_solve<double>(m, c, d.EaR[t], d.x0[t], w);
@@ -378,6 +401,32 @@ __global__ void k_ocp_batch(DevModel m, DevCtrl c, int64_t n, OcpBatch d, double
   d.kkt[3 * t + 0] = si.kkt_grad;
   d.kkt[3 * t + 1] = si.kkt_eq;
   d.kkt[3 * t + 2] = si.f;
+}
+
+// du_0/d(x_0, Q_z, R_u, Q_n) at given OCP solutions (one thread per OCP).
+__global__ void k_ocp_sens_batch(DevModel m, DevCtrl c, int64_t n, OcpBatch d, double* sens,
+                                 double* ws, int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int N = c.N;
+  const Ws w{ws + t, ld, N + 1};
+  const int64_t o1 = t * N, o2 = t * (N + 1);
+  for (int k = 0; k < N; ++k) {
+    w(U, k) = d.u[o1 + k];
+    w(LAM, k) = d.lam[o1 + k];
+    w(PIL, k) = d.pil[o1 + k];
+    w(PIU, k) = d.piu[o1 + k];
+  }
+  for (int k = 0; k <= N; ++k) {
+    w(X, k) = d.x[o2 + k];
+    w(ZB, k) = d.zbar[o2 + k];
+    if (k >= 1) w(VB, k) = Fss(m, d.EaR[t], w(ZB, k)) / c.Fconv;
+  }
+  w(X, 0) = d.x0[t];
+  double out[4];
+  const bool ok = ocp_sens(m, c, d.EaR[t], N, w, out);
+  for (int q = 0; q < 4; ++q) sens[t * 4 + q] = out[q];
+  d.info[t] = ok ? 0 : 1;
 }
 
 }  // namespace mc
@@ -506,6 +555,10 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
       return bad("threads_per_sm must be 0..2048");
     if (cc->nx_model != 0 && cc->nx_model != 1 && cc->nx_model != 3)
       return bad("nx_model must be 0, 1 or 3");
+    if (!(cc->Ru >= 0.0) || !(cc->Qn >= 0.0) || !std::isfinite(cc->Ru) || !std::isfinite(cc->Qn))
+      return bad("the objective weights Ru and Qn must be finite and >= 0");
+    if (cc->nx_model == 3 && (cc->Ru != 0.0 || cc->Qn != 0.0))
+      return bad("the three-state NMPC has the paper's objective only (Ru = Qn = 0)");
     if (cc->nx_model == 3 &&
         (cc->precision != MC_FP64 || cc->qp_solver != MC_QP_ACTIVE_SET ||
          cc->schedule != MC_SCHED_STATIC))
@@ -538,6 +591,9 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   c->u_scale = cc->u_scale; c->x_scale = cc->x_scale;
   c->N_min = cc->N_min; c->it_min = cc->sqp_max_it_min;
   c->nx_model = (cc->kind == MC_CTRL_NMPC && cc->nx_model == 3) ? 3 : 1;
+  c->Ru = (cc->kind == MC_CTRL_NMPC) ? cc->Ru : 0.0;
+  c->Qn = (cc->kind == MC_CTRL_NMPC) ? cc->Qn : 0.0;
+  c->r_scale = 2.0 * c->Ru * mm->Ts;
   if (cc->kind == MC_CTRL_NMPC) {
     c->Fconv = cc->u_scale / 60000.0;
     c->vmin = cc->u_min / cc->u_scale;
@@ -1126,6 +1182,59 @@ mc_status mc_pi_grad(mc_handle* h, int64_t j0, int64_t j1, int32_t checkpoint_ev
   return MC_OK;
 }
 
+mc_status mc_set_nmpc_weights(mc_handle* h, double Qz, double Ru, double Qn) {
+  if (!h) return MC_EINVAL;
+  if (h->c.kind != MC_CTRL_NMPC) return fail(h, MC_EINVAL, "mc_set_nmpc_weights needs an NMPC handle");
+  if (!(Qz >= 0.0) || !(Ru >= 0.0) || !(Qn >= 0.0) || !std::isfinite(Qz) || !std::isfinite(Ru) ||
+      !std::isfinite(Qn))
+    return fail(h, MC_EINVAL, "the weights must be finite and >= 0");
+  if (h->c.nx_model == 3 && (Ru != 0.0 || Qn != 0.0))
+    return fail(h, MC_EINVAL, "the three-state NMPC has the paper's objective only (Ru = Qn = 0)");
+  h->c.Qz = Qz;
+  h->c.Ru = Ru;
+  h->c.Qn = Qn;
+  h->c.r_scale = 2.0 * Ru * h->m.Ts;
+  drop_graphs(h);  // captured launches hold the old weights
+  return MC_OK;
+}
+
+mc_status mc_nmpc_grad(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) {
+  if (!h) return MC_EINVAL;
+  if (h->c.kind != MC_CTRL_NMPC) return fail(h, MC_EINVAL, "mc_nmpc_grad needs an NMPC handle");
+  if (h->c.precision != MC_FP64 || h->c.nx_model == 3)
+    return fail(h, MC_EINVAL, "mc_nmpc_grad runs the one-state NMPC in FP64");
+  if (j0 < 0 || j1 < j0 || j1 > h->n_sims) return fail(h, MC_EINVAL, "bad trajectory range");
+  if (!h->dphi) {
+    if (cudaMalloc((void**)&h->dphi, sizeof(double) * 3 * (h->n_sims > 0 ? h->n_sims : 1)) !=
+            cudaSuccess ||
+        cudaMalloc((void**)&h->gmean, sizeof(double) * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MC_ENOMEM, "cudaMalloc failed for the gradient buffers");
+    }
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  MC_CUDA(h, cudaEventRecord(h->ev0, st));
+  const cudaStream_t ls = fork_stream(h, st);
+  if (j1 > j0) {
+    const int64_t n = j1 - j0;
+    const int64_t threads = n < h->ws_ld ? n : h->ws_ld;
+    const int64_t blocks = (threads + kNmpcThreads - 1) / kNmpcThreads;
+    k_nmpc_grad<<<(unsigned)blocks, kNmpcThreads, 0, ls>>>(h->m, h->c, j0, j1, h->phi, h->cnt,
+                                                           h->dphi, h->ws, h->ws_ld);
+  }
+  k_grad_mean<<<1, kGradThreads, 0, ls>>>(h->phi, h->dphi, j0, j1, h->gmean);
+  const mc_status s = launch_stats(h, j0, j1, ls);
+  join_stream(h, st, ls);
+  MC_CUDA(h, cudaGetLastError());
+  if (s != MC_OK) return s;
+  MC_CUDA(h, cudaEventRecord(h->ev1, st));
+  h->ran = true;
+  h->grad_ran = true;
+  h->last_j0 = j0;
+  h->last_j1 = j1;
+  return MC_OK;
+}
+
 mc_status mc_grad_mean(mc_handle* h, double out[3], int64_t timeout_ms) {
   if (!h || !out) return MC_EINVAL;
   if (!h->grad_ran) return fail(h, MC_ENOTRUN, "mc_pi_grad has not been called");
@@ -1327,6 +1436,63 @@ mc_status mc_ocp_solve_batch(const mc_model_t* model, const mc_controller_t* ctr
     if (e == cudaSuccess) e = cudaMemcpy(info, di, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(kkt, d.kkt, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_ocp_solve_batch");
+  }
+  for (void* p : owned) cudaFree(p);
+  return s;
+}
+
+mc_status mc_ocp_sens_batch(const mc_model_t* model, const mc_controller_t* ctrl, int64_t n,
+                            const double* x0, const double* EaR, const double* zbar,
+                            const double* u, const double* x, const double* lam,
+                            const double* pil, const double* piu, double* sens,
+                            int32_t* status) {
+  if (n < 0 || (n > 0 && (!x0 || !EaR || !zbar || !u || !x || !lam || !pil || !piu || !sens ||
+                          !status)))
+    return fail(nullptr, MC_EINVAL, "mc_ocp_sens_batch: bad arguments");
+  DevModel m;
+  DevCtrl c;
+  std::string why;
+  if (fill_dev(model, ctrl, 0, &m, &c, &why) != MC_OK) return fail(nullptr, MC_EINVAL, why);
+  if (c.kind != MC_CTRL_NMPC || c.nx_model == 3)
+    return fail(nullptr, MC_EINVAL, "mc_ocp_sens_batch: one-state NMPC controller needed");
+  if (n == 0) return MC_OK;
+  const int N = c.N;
+  const size_t n1 = (size_t)n * N, n2 = (size_t)n * (N + 1);
+  OcpBatch d{};
+  std::vector<void*> owned;
+  bool ok = true;
+  auto up = [&](const double** dst, const double* src, size_t cnt) {
+    double* p = nullptr;
+    ok = ok && to_dev(&p, src, cnt);
+    owned.push_back(p);
+    *dst = p;
+  };
+  auto upm = [&](double** dst, const double* src, size_t cnt) {
+    double* p = nullptr;
+    ok = ok && to_dev(&p, src, cnt);
+    owned.push_back(p);
+    *dst = p;
+  };
+  up(&d.x0, x0, n); up(&d.EaR, EaR, n); up(&d.zbar, zbar, n2);
+  upm(&d.u, u, n1); upm(&d.x, x, n2); upm(&d.lam, lam, n1); upm(&d.pil, pil, n1);
+  upm(&d.piu, piu, n1);
+  int32_t* dinfo = nullptr;
+  double *dsens = nullptr, *ws = nullptr;
+  ok = ok && to_dev<int32_t>(&dinfo, nullptr, n) && to_dev<double>(&dsens, nullptr, 4 * n) &&
+       to_dev<double>(&ws, nullptr, (size_t)kNArr * (N + 1) * n);
+  owned.push_back(dinfo);
+  owned.push_back(dsens);
+  owned.push_back(ws);
+  d.info = dinfo;
+  mc_status s = MC_OK;
+  if (!ok) {
+    s = fail(nullptr, MC_ENOMEM, "mc_ocp_sens_batch: allocation");
+  } else {
+    k_ocp_sens_batch<<<(unsigned)((n + 127) / 128), 128>>>(m, c, n, d, dsens, ws, n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(sens, dsens, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(status, dinfo, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_ocp_sens_batch");
   }
   for (void* p : owned) cudaFree(p);
   return s;

@@ -142,6 +142,8 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
   }
   ekf_filter(m, y, T.xhat, T.P);
   for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(T.i + k) * m.Ts);
+  if (c.Ru != 0.0)
+    for (int k = 1; k <= N; ++k) w(VB, k) = Fss(m, T.tp.EaR_c, w(ZB, k)) / c.Fconv;
   sqp_start<R>(m, c, T.tp.EaR_c, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s);
   return true;
 }

@@ -1,0 +1,332 @@
+// mc_grad_nmpc.cuh -- gradient of Phi_j with respect to the NMPC weights
+// (Q_z, R_u, Q_n) of the extended objective, through the closed loop.
+//
+// Model of the derivative: every OCP is represented by its solution map
+// u_0 = U(x-hat_{i|i}, theta) at the KKT point the SQP returns, differentiated
+// implicitly (the tangent of a KKT point solves the equality-constrained QP
+// whose Hessian is that of the Lagrangian and whose linear term is the
+// derivative of the Lagrangian gradient with respect to the parameter, with
+// the active bounds held); the plant (Euler-Maruyama), the measurement and
+// the CD-EKF (prediction and Joseph filter) are differentiated exactly, in
+// forward mode, three directions at once.  The warm start of the next OCP does
+// not enter (the KKT point does not depend on it).  FP64, one thread per
+// trajectory, the static schedule.
+#pragma once
+
+#include "mc_closedloop.cuh"
+#include "mc_nmpc3.cuh"
+
+namespace mc {
+
+// One-state model with second derivatives: f, f_x, f_F, f_xx, f_xF.
+//   f = F (T_in - c_T) + beta r(c_T) V,  c_T = x / V,  r = k c_A c_B,
+//   k = k0 exp(-E/c_T), c_A = c_A,in + (T_in - c_T)/beta, c_B = c_B,in + 2 (T_in - c_T)/beta;
+//   f_x = (-F + beta V r') / V, f_xx = beta r'' / V, f_F = T_in - c_T, f_xF = -1/V,
+//   r' = k' c_A c_B + k (c_A' c_B + c_A c_B'),
+//   r'' = k'' c_A c_B + 2 k' (c_A' c_B + c_A c_B') + 2 k c_A' c_B',
+//   k' = k E / c_T^2, k'' = k E (E - 2 c_T) / c_T^4.
+__device__ __forceinline__ void model1_d2(const DevModel& m, double EaR, double x, double F,
+                                          double& f, double& fx, double& fF, double& fxx,
+                                          double& fxF) {
+  const double V = m.V, beta = m.beta, Tin = m.T_in;
+  const double cT = x / V;
+  const double cA = m.cA_in + (Tin - cT) / beta, cB = m.cB_in + 2.0 * (Tin - cT) / beta;
+  const double dA = -1.0 / beta, dB = -2.0 / beta;
+  const double k = m.k0 * expr(-EaR / cT);
+  const double k1 = k * EaR / (cT * cT);
+  const double k2 = k * EaR * (EaR - 2.0 * cT) / (cT * cT * cT * cT);
+  const double r = k * cA * cB;
+  const double r1 = k1 * cA * cB + k * (dA * cB + cA * dB);
+  const double r2 = k2 * cA * cB + 2.0 * k1 * (dA * cB + cA * dB) + 2.0 * k * dA * dB;
+  f = F * (Tin - cT) + beta * r * V;
+  fx = (-F + beta * V * r1) / V;
+  fF = Tin - cT;
+  fxx = beta * r2 / V;
+  fxF = -1.0 / V;
+}
+
+// One shooting interval (n_rk4 RK4 steps) with first- and second-order
+// forward sensitivities of the end state with respect to x0 and v, obtained
+// by differentiating every RK4 stage twice.
+__device__ __noinline__ void rk4_interval_d2(const DevModel& m, double EaR, int n_rk4, double Ts,
+                                             double x0, double v, double Fconv, double& xF,
+                                             double& a, double& b, double& aa, double& ab,
+                                             double& bb) {
+  const double h = Ts / (double)n_rk4;
+  const double F = v * Fconv;
+  double x = x0;
+  a = 1.0;
+  b = 0.0;
+  aa = ab = bb = 0.0;
+  for (int s = 0; s < n_rk4; ++s) {
+    double Kx = 0, Ka = 0, Kb = 0, Kaa = 0, Kab = 0, Kbb = 0;        // previous stage
+    double Sx = 0, Sa = 0, Sb = 0, Saa = 0, Sab = 0, Sbb = 0;        // weighted sums
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const double c = (st == 0) ? 0.0 : ((st == 3) ? h : 0.5 * h);
+      const double X = x + c * Kx, Xa = a + c * Ka, Xb = b + c * Kb;
+      const double Xaa = aa + c * Kaa, Xab = ab + c * Kab, Xbb = bb + c * Kbb;
+      double f, fx, fF, fxx, fxF;
+      model1_d2(m, EaR, X, F, f, fx, fF, fxx, fxF);
+      Kx = f;
+      Ka = fx * Xa;
+      Kb = fx * Xb + fF * Fconv;
+      Kaa = fxx * Xa * Xa + fx * Xaa;
+      Kab = fxx * Xa * Xb + fxF * Fconv * Xa + fx * Xab;
+      Kbb = fxx * Xb * Xb + 2.0 * fxF * Fconv * Xb + fx * Xbb;
+      const double wgt = (st == 0 || st == 3) ? 1.0 : 2.0;
+      Sx += wgt * Kx;
+      Sa += wgt * Ka;
+      Sb += wgt * Kb;
+      Saa += wgt * Kaa;
+      Sab += wgt * Kab;
+      Sbb += wgt * Kbb;
+    }
+    const double h6 = h / 6.0;
+    x += h6 * Sx;
+    a += h6 * Sa;
+    b += h6 * Sb;
+    aa += h6 * Saa;
+    ab += h6 * Sab;
+    bb += h6 * Sbb;
+  }
+  xF = x;
+}
+
+// du_0 / d(x_0, Q_z, R_u, Q_n) at the KKT point in (U, X, LAM, PIL, PIU) with
+// x_0 in X(., 0), set-points in ZB and steady-state inputs in VB (needed for
+// the R_u direction whatever R_u is).  Backward Riccati sweep of the tangent QP with the exact
+// Lagrangian Hessian and four right-hand sides; only u_0 is needed, so there
+// is no forward sweep.  A bound is active when u_k lies on it and its
+// multiplier exceeds 1e-10.  Returns false (and zeros) when a pivot of a free
+// input is not positive (the reduced Hessian is not positive definite).
+__device__ bool ocp_sens(const DevModel& m, const DevCtrl& c, double EaR, int N, const Ws& w,
+                        double out[4]) {
+  const double xs = c.x_scale, Ts = m.Ts, sz = xs / m.V;
+  double P = (2.0 * Ts * c.Qz + 2.0 * c.Qn) * sz * sz;
+  double p[4];
+  {
+    const double dzN = w(X, N) * sz - w(ZB, N);
+    p[0] = 0.0;
+    p[1] = 2.0 * Ts * dzN * sz;
+    p[2] = 0.0;
+    p[3] = 2.0 * dzN * sz;
+  }
+  for (int k = N - 1; k >= 0; --k) {
+    const double xk = w(X, k), uk = w(U, k), lam = w(LAM, k);
+    double xF, a, b, aa, ab, bb;
+    rk4_interval_d2(m, EaR, c.n_rk4, Ts, xk * xs, uk, c.Fconv, xF, a, b, aa, ab, bb);
+    const double A = a, B = b / xs, Fxx = aa * xs, Fxu = ab, Fuu = bb / xs;
+    const double Huu = 2.0 * Ts * c.Ru - lam * Fuu;
+    const double Hxu = -lam * Fxu;
+    const double Hxx = 2.0 * Ts * c.Qz * sz * sz - lam * Fxx;
+    // linear terms of the four directions at stage k, and the offset of the
+    // first dynamics row (dx_1 = A_0 dx_0 + B_0 du_0)
+    double cu[4] = {0.0, 0.0, 0.0, 0.0}, cx[4] = {0.0, 0.0, 0.0, 0.0}, bo[4] = {0, 0, 0, 0};
+    cu[2] = 2.0 * Ts * (uk - w(VB, k + 1));
+    if (k == 0) {
+      cu[0] = Hxu;          // x_0 cross term, dx_0 = 1 in direction 0
+      bo[0] = A;
+    } else {
+      const double dz = xk * sz - w(ZB, k);
+      cx[1] = 2.0 * Ts * dz * sz;
+    }
+    const bool act = (uk - c.vmin <= 1e-12 && w(PIL, k) > 1e-10) ||
+                     (c.vmax - uk <= 1e-12 && w(PIU, k) > 1e-10);
+    double Pn, pn[4];
+    if (act) {
+      // du_k = 0
+      Pn = ((k > 0) ? Hxx : 0.0) + ((k > 0) ? A * A * P : 0.0);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        pn[d] = cx[d] + ((k > 0) ? A * (P * bo[d] + p[d]) : 0.0);
+        if (k == 0) out[d] = 0.0;
+      }
+    } else {
+      const double Rb = Huu + B * B * P;
+      if (!(Rb > 0.0)) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) out[d] = 0.0;
+        return false;
+      }
+      const double iR = 1.0 / Rb;
+      const double Sb = (k > 0) ? Hxu + A * P * B : 0.0;
+      Pn = (k > 0) ? Hxx + A * A * P - Sb * Sb * iR : 0.0;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const double Pbp = P * bo[d] + p[d];
+        const double sb = cu[d] + B * Pbp;
+        if (k == 0) out[d] = -sb * iR;
+        pn[d] = (k > 0) ? cx[d] + A * Pbp - Sb * sb * iR : 0.0;
+      }
+    }
+    P = Pn;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) p[d] = pn[d];
+  }
+  return true;
+}
+
+// Tangent of the CD-EKF prediction (RK4 on x' = f, P' = 2 f_x P + (F s_T)^2)
+// in three directions, from (x, P) with tangents (dx, dP) and input tangent dF.
+__device__ void ekf_predict_tan(const DevModel& m, double EaR, int n_rk4, double F, double x,
+                                double P, const double dF[3], double dx[3], double dP[3]) {
+  const double h = m.Ts / (double)n_rk4, hh = 0.5 * h, h6 = h / 6.0;
+  const double sT = m.sigma[2];
+  const double q = F * sT * F * sT;
+  double dq[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dq[d] = 2.0 * F * sT * sT * dF[d];
+  for (int s = 0; s < n_rk4; ++s) {
+    double fs = 0, ps = 0, kx = 0, kp = 0;
+    double dfs[3] = {0, 0, 0}, dps[3] = {0, 0, 0}, dkx[3] = {0, 0, 0}, dkp[3] = {0, 0, 0};
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const double cst = (st == 0) ? 0.0 : ((st == 3) ? h : hh);
+      const double X = x + cst * kx, PP = P + cst * kp;
+      double f, fx, fF, fxx, fxF;
+      model1_d2(m, EaR, X, F, f, fx, fF, fxx, fxF);
+      const double pk = 2.0 * fx * PP + q;
+      const double wgt = (st == 0 || st == 3) ? 1.0 : 2.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double dX = dx[d] + cst * dkx[d], dPP = dP[d] + cst * dkp[d];
+        const double dfv = fx * dX + fF * dF[d];
+        const double dfx = fxx * dX + fxF * dF[d];
+        const double dpk = 2.0 * dfx * PP + 2.0 * fx * dPP + dq[d];
+        dkx[d] = dfv;
+        dkp[d] = dpk;
+        dfs[d] += wgt * dfv;
+        dps[d] += wgt * dpk;
+      }
+      kx = f;
+      kp = pk;
+      fs += wgt * f;
+      ps += wgt * pk;
+    }
+    x += h6 * fs;
+    P += h6 * ps;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dx[d] += h6 * dfs[d];
+      dP[d] += h6 * dps[d];
+    }
+  }
+}
+
+// Tangent of the Joseph-form filter with y = x/V + v: x, P before the update.
+__device__ __forceinline__ void ekf_filter_tan(const DevModel& m, double y, double x, double P,
+                                               const double dy[3], double dx[3], double dP[3]) {
+  const double R = m.meas_sd * m.meas_sd, C = 1.0 / m.V;
+  const double e = y - x / m.V;
+  const double Re = R + C * P * C;
+  const double K = P * C / Re;
+  const double ImKC = 1.0 - K * C;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double de = dy[d] - dx[d] / m.V;
+    const double dRe = C * C * dP[d];
+    const double dK = (dP[d] * C * Re - P * C * dRe) / (Re * Re);
+    const double dImKC = -dK * C;
+    const double dPn = 2.0 * ImKC * dImKC * P + ImKC * ImKC * dP[d] + 2.0 * K * dK * R;
+    dx[d] = dx[d] + dK * e + K * de;
+    dP[d] = dPn;
+  }
+}
+
+// Tangent of one sample of the plant (N_s Euler-Maruyama substeps from n with
+// flow F) in three directions: dn (3 directions x 3 states), dF per direction.
+__device__ void plant_interval_tan(const DevModel& m, const TrajParams& tp, uint32_t j, int i,
+                                   double F, const double dF[3], const double n_in[3],
+                                   double dn[3][3]) {
+  const double h = m.Ts / (double)m.n_em, sqh = sqrt(h);
+  double n[3] = {n_in[0], n_in[1], n_in[2]};
+  for (int s = 0; s < m.n_em; ++s) {
+    const int64_t ks = (int64_t)i * m.n_em + s;
+    const double tau = m.t0 + (double)ks * h;
+    const double Tin = (m.dTin != 0.0 && tau >= tp.t_d) ? m.T_in + tp.dTin : m.T_in;
+    double xi[3];
+    process_noise<double>(m, j, (uint32_t)ks, xi);
+    double f[3], J[9], fF[3];
+    drift3(m, tp.EaR, Tin, n, F, f, J, fF);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double nd[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        double s2 = fF[p] * dF[d];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s2 += J[p * 3 + q] * dn[d][q];
+        nd[p] = dn[d][p] + h * s2 + dF[d] * m.sigma[p] * sqh * xi[p];
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) dn[d][p] = nd[p];
+    }
+    em_step<double>(m, tp.EaR, Tin, n, F, h, sqh, xi);
+  }
+}
+
+// The closed loop of the NMPC (static schedule, FP64) with the tangents of
+// Phi_j in the directions (Q_z, R_u, Q_n).  cnt[7] also counts the OCPs whose
+// sensitivity could not be formed (their input tangent is taken as 0).
+__device__ TrajOut traj_nmpc_grad(const DevModel& m, const DevCtrl& c, uint32_t j, const Ws& w,
+                                  double dphi[3]) {
+  NmpcTraj T;
+  SqpState s;
+  nmpc_begin(m, c, j, w, T);
+  double dn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double dxh[3] = {0, 0, 0}, dPh[3] = {0, 0, 0}, dFp[3] = {0, 0, 0}, dph[3] = {0, 0, 0};
+  const int K = m.n_steps;
+  for (;;) {
+    // tangents of this sample's Phi term, measurement and CD-EKF; the values
+    // they start from are the ones nmpc_sample uses
+    const double t_i = m.t0 + (double)T.i * m.Ts;
+    const double cT = T.n[2] / m.V;
+    const double xh0 = T.xhat, Ph0 = T.P, Fp = T.F_prev;
+    const int i = T.i;
+    if (isfinite(cT)) {
+      const double zi = zbar(m, t_i);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dph[d] += 2.0 * (cT - zi) * dn[d][2] / m.V;
+    }
+    if (!nmpc_sample<double>(m, c, w, T, s)) break;
+    if (c.Ru == 0.0)  // the R_u direction needs the steady-state inputs
+      for (int k = 1; k <= T.tp.N; ++k) w(VB, k) = Fss(m, T.tp.EaR_c, w(ZB, k)) / c.Fconv;
+    double dy[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dy[d] = dn[d][2] / m.V;
+    double xp = xh0, Pp = Ph0;
+    if (i > 0) {
+      ekf_predict_tan(m, T.tp.EaR_c, c.n_rk4, Fp, xh0, Ph0, dFp, dxh, dPh);
+      ekf_predict<double>(m, T.tp.EaR_c, c.n_rk4, Fp, xp, Pp);
+    }
+    const double y = cT + m.meas_sd * meas_noise<double>(m, T.j, (uint32_t)i);
+    ekf_filter_tan(m, y, xp, Pp, dy, dxh, dPh);
+    // the OCP
+    while (!sqp_check<double>(c, w, s)) {
+      int r;
+      do {
+        sqp_eval_trial<double>(m, c, T.tp.EaR_c, w, s);
+        r = sqp_trial_result<double>(c, w, s);
+      } while (r == 2);
+      if (r == 1) break;
+    }
+    double S[4];
+    if (!ocp_sens(m, c, T.tp.EaR_c, T.tp.N, w, S)) s.info.qp_fail++;
+    double dF[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dF[d] = (S[0] * dxh[d] / c.x_scale + S[1 + d]) * c.Fconv;
+    const double F = w(U, 0) * c.Fconv;
+    plant_interval_tan(m, T.tp, T.j, i, F, dF, T.n, dn);
+    nmpc_apply<double>(m, c, w, T, s.info);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dFp[d] = dF[d];
+  }
+  const TrajOut out = T.out;
+  const double wK = 1.0 / (double)(K + 1);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dphi[d] = isfinite(out.phi) ? dph[d] * wK : nan("");
+  return out;
+}
+
+}  // namespace mc

@@ -34,6 +34,7 @@ enum Arr : int {
   RP, RPP, RK, RKF, RZ,           // Riccati factors P_{k+1}, p_{k+1}, K_k, k_k; trial du
   TL, TU, ZL, ZU, DUA, RIR, RSB,  // IPM slacks, duals, affine du, 1/Rbar, Sbar
   DXS, DMS,                       // IPM step in dx and mu
+  VB,                             // steady-state inputs vbar_k of the set-points (R_u term)
   kNArr
 };
 

@@ -92,6 +92,18 @@ __device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, dou
     w(q_arr, k + 1) = qf * dz;
     xk = xn;
   }
+  // extended objective: R_u (v_k - vbar_{k+1})^2 T_s and Q_n (z_N - zbar_N)^2
+  if (c.Ru != 0.0) {
+    for (int k = 0; k < N; ++k) {
+      const double dv = w(u_arr, k) - w(VB, k + 1);
+      f += c.Ru * dv * dv * m.Ts;
+    }
+  }
+  if (c.Qn != 0.0) {
+    const double dz = w(x_arr, N) * xs * m.iV - w(ZB, N);
+    f += c.Qn * dz * dz;
+    w(q_arr, N) += 2.0 * c.Qn * dz * xs * m.iV;
+  }
   return f;
 }
 
@@ -165,10 +177,14 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
   const int N = s.N;
   const double s_max = 100.0;
   double kg = 0.0, ke = 0.0, mult1 = 0.0;
+  const bool has_r = (c.Ru != 0.0);
+  if (has_r)  // input gradient r_k = 2 R_u (v_k - vbar_{k+1}) T_s at the current point
+    for (int k = 0; k < N; ++k) w(QR, k) = c.r_scale * (w(U, k) - w(VB, k + 1));
   for (int k = 0; k < N; ++k) {
     const double lam = w(LAM, k), pil = w(PIL, k), piu = w(PIU, k);
     mult1 += fabs(lam) + fabs(pil) + fabs(piu);
-    const double gu = -lam * w(EB, k) - pil + piu;
+    double gu = -lam * w(EB, k) - pil + piu;
+    if (has_r) gu += w(QR, k);
     double gx;
     if (k + 1 < N)
       gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
@@ -242,8 +258,8 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
     w(LB, k) = c.vmin - u;
     w(UB, k) = c.vmax - u;
   }
-  const QpResult qr = (c.qp_solver == 1) ? qp_ipm(w, N, false, c.ip_max_it, c.ip_tol)
-                                         : qp_active_set(w, N, false, 10 * N + 20);
+  const QpResult qr = (c.qp_solver == 1) ? qp_ipm(w, N, has_r, c.ip_max_it, c.ip_tol)
+                                         : qp_active_set(w, N, has_r, 10 * N + 20);
   s.info.qp_iters += qr.iters;
   if (qr.status != 0) s.info.qp_fail++;
   s.info.iters++;
@@ -256,6 +272,7 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
     w(SIG, k) = sg;
     pen += sg * fabs(w(EG, k));
     dfd += w(EQ, k + 1) * w(DX, k + 1);
+    if (has_r) dfd += w(QR, k) * w(DU, k);
   }
   s.T0 = s.f + pen;
   s.DT0 = dfd - pen;
@@ -331,6 +348,7 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
   for (int k = 0; k < N; ++k) {
     const double lam = w(LAM, k);
     w(GLU, k) = -lam * w(EB, k) - w(PIL, k) + w(PIU, k);
+    if (c.Ru != 0.0) w(GLU, k) += w(QR, k);   // r at the old point
     double gx;
     if (k + 1 < N)
       gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;

@@ -53,7 +53,7 @@ class McController(C.Structure):
                 ("ip_max_it", C.c_int32), ("ip_tol", C.c_double), ("u_scale", C.c_double),
                 ("x_scale", C.c_double), ("N_min", C.c_int32), ("sqp_max_it_min", C.c_int32),
                 ("schedule", C.c_int32), ("threads_per_sm", C.c_int32),
-                ("nx_model", C.c_int32)]
+                ("nx_model", C.c_int32), ("Ru", C.c_double), ("Qn", C.c_double)]
 
 
 class McStats(C.Structure):
@@ -116,6 +116,13 @@ def lib():
             L.mc_autotune.argtypes = [H, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
             L.mc_set_sm_partition.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
             L.mc_set_sm_partition.restype = C.c_int
+            L.mc_set_nmpc_weights.argtypes = [H, C.c_double, C.c_double, C.c_double]
+            L.mc_set_nmpc_weights.restype = C.c_int
+            L.mc_nmpc_grad.argtypes = [H, C.c_int64, C.c_int64, C.c_void_p]
+            L.mc_nmpc_grad.restype = C.c_int
+            L.mc_ocp_sens_batch.argtypes = ([C.POINTER(McModel), C.POINTER(McController),
+                                              C.c_int64] + [_dp] * 9 + [_ip])
+            L.mc_ocp_sens_batch.restype = C.c_int
             L.mc_exp_batch.argtypes = [_dp, C.c_int64, _dp]
             L.mc_exp_batch.restype = C.c_int
             L.mc_set_pi_gains.argtypes = [H, C.c_double, C.c_double, C.c_double]
@@ -180,6 +187,8 @@ def make_ctrl(cd: dict) -> McController:
     c.schedule = SCHEDULES[cd.get("schedule", "static")]
     c.threads_per_sm = int(cd.get("threads_per_sm", 0))
     c.nx_model = int(cd.get("nx_model", 1))
+    c.Ru = float(cd.get("Ru", 0.0))
+    c.Qn = float(cd.get("Qn", 0.0))
     return c
 
 
@@ -293,6 +302,14 @@ class MonteCarlo:
         _check(lib().mc_pi_grad(self._h, j0, j1, int(checkpoint_every), _stream_ptr(stream)),
                self._h)
 
+    def set_nmpc_weights(self, Qz: float, Ru: float, Qn: float):
+        _check(lib().mc_set_nmpc_weights(self._h, float(Qz), float(Ru), float(Qn)), self._h)
+
+    def nmpc_grad(self, stream=None, j0: int = 0, j1: int | None = None):
+        """Closed loop with the tangents of Phi in (Q_z, R_u, Q_n) (asynchronous)."""
+        j1 = self.n_sims if j1 is None else j1
+        _check(lib().mc_nmpc_grad(self._h, j0, j1, _stream_ptr(stream)), self._h)
+
     def grad_mean(self, timeout_ms: int = 0) -> np.ndarray:
         """Mean dPhi/d(k_P, k_I, k_aw) over the finite trajectories of the last pi_grad."""
         g = np.zeros(3)
@@ -313,6 +330,23 @@ class MonteCarlo:
 
 
 # ------------------------------------------------------------------ building blocks
+
+def ocp_sens_batch(model: dict, ctrl: dict, x0, EaR, zbar, u, x, lam, pil, piu):
+    """du_0/d(x_0, Q_z, R_u, Q_n) at given OCP solutions; returns (sens n x 4, status)."""
+    L = lib()
+    m, keep = make_model(model)
+    c = make_ctrl(ctrl)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.shape[0]
+    arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shp))
+            for a, shp in ((x0, (n,)), (EaR, (n,)), (zbar, (n, c.N + 1)), (u, (n, c.N)),
+                           (x, (n, c.N + 1)), (lam, (n, c.N)), (pil, (n, c.N)), (piu, (n, c.N)))]
+    sens = np.zeros((n, 4))
+    st = np.zeros(n, dtype=np.int32)
+    _check(L.mc_ocp_sens_batch(C.byref(m), C.byref(c), n, *[_p(a) for a in arrs], _p(sens),
+                               st.ctypes.data_as(_ip)))
+    return sens, st
+
 
 def exp_batch(x):
     """The device FP64 exponential of the rate law, elementwise on x."""

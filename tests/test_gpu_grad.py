@@ -152,3 +152,139 @@ def test_edge_cases_and_errors():
     with pytest.raises(mc.McError):
         hm.pi_grad(20)
     hm.close()
+
+
+# ------------------------------------------------------------------ NMPC weights
+
+from paper_2212_02197_gb300.autograd import nmpc_mean_phi  # noqa: E402
+
+WN = "cstr_100x120_N20_fp64"
+
+
+def _ocp_cases(n, N, rng):
+    """OCPs from the oracle's SQP whose first input is interior."""
+    m = W.model(240)
+    c = dict(W.nmpc(N), Ru=0.3, Qn=2.0)
+    out = []
+    while len(out) < n:
+        z = rng.choice([282.0, 290.0, 300.0, 340.0])
+        x0 = z + rng.uniform(0.2, 2.0)
+        zb = np.full(N + 1, z)
+        u, x, lam, pil, piu, info = oracle.sqp(m, c, m["EaR"], x0, zb, np.full(N, 0.5),
+                                               np.full(N + 1, x0))
+        if info["status"] == 0 and 0.0 < u[0] < 1.0:
+            out.append((x0, zb, u, x, lam, pil, piu))
+    return m, c, out
+
+
+def test_ocp_sensitivity_matches_oracle():
+    """The GPU's second-order shooting sensitivities and Riccati sweep against
+    the oracle's difference Hessian and dense KKT solve, on the same KKT
+    points."""
+    rng = np.random.default_rng(21)
+    N = 20
+    m, c, cases = _ocp_cases(24, N, rng)
+    cols = list(zip(*cases))
+    sens, st = mc.ocp_sens_batch(m, c, np.array(cols[0]), m["EaR"], np.array(cols[1]),
+                                 np.array(cols[2]), np.array(cols[3]), np.array(cols[4]),
+                                 np.array(cols[5]), np.array(cols[6]))
+    assert np.all(st == 0)
+    for i, (x0, zb, u, x, lam, pil, piu) in enumerate(cases):
+        s_ok, ref = oracle.ocp_sens(m, c, m["EaR"], x0, zb, u, x, lam, pil, piu)
+        assert s_ok == 0
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(sens[i], ref, rtol=1e-5, atol=1e-7 * scale)
+
+
+def test_nmpc_grad_matches_oracle_per_trajectory():
+    w = W.get(WN)
+    m = dict(w["model"], n_steps=40)
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+    n = 48
+    h = mc.MonteCarlo(m, c, n, w["seed"])
+    h.nmpc_grad()
+    st = h.stats(timeout_ms=600000)
+    phi, g, cnt = h.phi(), h.grad(), h.counters()
+    h.close()
+    rphi, rg, fails = oracle.nmpc_grad(m, c, w["seed"], 0, n)
+    ok = (cnt["n_ocp_failed"] == 0) & (fails == 0)
+    assert ok.sum() >= 0.9 * n
+    np.testing.assert_allclose(phi[ok], rphi[ok], rtol=1e-6)
+    scale = np.abs(rg[ok]).max(axis=0)
+    err = np.abs(g[ok] - rg[ok]) / (np.abs(rg[ok]) + 1e-3 * scale)
+    assert err.max() < 1e-3, err.max()
+    assert st["n_nonfinite"] == 0
+
+
+def test_nmpc_grad_phi_equals_the_static_run():
+    w = W.get(WN)
+    m = dict(w["model"], n_steps=40)
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+    h = mc.MonteCarlo(m, c, 128, w["seed"])
+    h.nmpc_grad()
+    h.sync()
+    phi = h.phi()
+    h.run()
+    h.sync()
+    assert np.array_equal(h.phi(), phi)
+    h.close()
+
+
+def test_nmpc_mean_gradient_matches_central_differences():
+    """The tangent is the derivative of the closed loop whose OCPs sit exactly
+    at their KKT points.  An SQP stopped at a finite tolerance lags that map
+    (its input moves less than the solution would), so central differences of
+    the simulated Phi approach the tangent as the tolerance tightens: about
+    15 % apart at 1e-5, 10 % at 1e-6, a few percent at 1e-7 (measured with the
+    oracle).  Here: OCPs solved to 1e-7, steps of 1e-2 of each weight, means
+    over the trajectories whose OCPs all converged in every run."""
+    w = W.get(WN)
+    m = dict(w["model"], n_steps=24)
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, sqp_tol=1e-7, sqp_max_it=300, schedule="static")
+    n = 2000
+    h = mc.MonteCarlo(m, c, n, w["seed"])
+    h.nmpc_grad()
+    h.sync()
+    g = h.grad()
+    ok = h.counters()["n_ocp_failed"] == 0
+    runs = {}
+    for k in ("Qz", "Ru", "Qn"):
+        hk = 1e-2 * c[k]
+        for sgn in (1, -1):
+            ww = dict(Qz=c["Qz"], Ru=c["Ru"], Qn=c["Qn"])
+            ww[k] += sgn * hk
+            h.set_nmpc_weights(ww["Qz"], ww["Ru"], ww["Qn"])
+            h.run()
+            h.sync()
+            runs[(k, sgn)] = h.phi()
+            ok &= h.counters()["n_ocp_failed"] == 0
+    h.close()
+    assert ok.sum() >= 0.5 * n
+    for q, k in enumerate(("Qz", "Ru", "Qn")):
+        hk = 1e-2 * c[k]
+        fd = (runs[(k, 1)][ok] - runs[(k, -1)][ok]) / (2 * hk)
+        assert fd.mean() == pytest.approx(g[ok, q].mean(), rel=5e-2), (k, fd.mean(), g[ok, q].mean())
+
+
+def test_nmpc_autograd_and_errors():
+    w = W.get(WN)
+    m = dict(w["model"], n_steps=24)
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+    h = mc.MonteCarlo(m, c, 256, w["seed"])
+    x = torch.tensor([1.0, 0.2, 1.0], dtype=torch.float64, requires_grad=True)
+    y = nmpc_mean_phi(x, h)
+    y.backward()
+    assert torch.allclose(x.grad, torch.tensor(h.grad_mean(), dtype=torch.float64), rtol=0, atol=0)
+    with pytest.raises(mc.McError):
+        h.set_nmpc_weights(-1.0, 0.0, 0.0)
+    h.close()
+    hp = mc.MonteCarlo(m, w["pi"], 4, w["seed"])
+    with pytest.raises(mc.McError):
+        hp.nmpc_grad()
+    with pytest.raises(mc.McError):
+        hp.set_nmpc_weights(1.0, 0.0, 0.0)
+    hp.close()
+    hm = mc.MonteCarlo(m, dict(c, precision="mixed", sqp_tol=1e-3, ls_max=3), 4, w["seed"])
+    with pytest.raises(mc.McError):
+        hm.nmpc_grad()
+    hm.close()

@@ -168,6 +168,38 @@ def test_ocp_sqp_matches_oracle(N):
     assert agree >= 0.8 * n
 
 
+@pytest.mark.parametrize("Ru,Qn", [(0.5, 0.0), (0.0, 4.0), (2.0, 1.0)])
+def test_weighted_ocp_matches_oracle(Ru, Qn):
+    """The extended objective (input-deviation and terminal weights)."""
+    rng = np.random.default_rng(11)
+    N, n = 20, 64
+    c = dict(W.nmpc(N), Ru=Ru, Qn=Qn)
+    m, x0, zbar, u, x = ocp_cases(n, N, rng)
+    dev = mc.ocp_solve_batch(m, c, x0, m["EaR"], zbar, u, x)
+    agree = 0
+    for i in range(n):
+        ru, rx, rl, _, _, info = oracle.sqp(dict(m), c, m["EaR"], x0[i], zbar[i], u[i], x[i])
+        if info["status"] == 0 and dev["status"][i] == 0:
+            agree += 1
+            assert np.allclose(dev["u"][i], ru, rtol=0, atol=1e-5), i
+            assert dev["f"][i] == pytest.approx(info["f"], rel=1e-6, abs=1e-9)
+    assert agree >= 0.9 * n
+
+
+def test_weighted_closed_loop_matches_oracle():
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=60)
+    for sched in ("persistent", "static"):
+        c = dict(w["nmpc"], Ru=0.5, Qn=2.0, schedule=sched)
+        h = mc.MonteCarlo(m, c, 64, w["seed"])
+        h.run()
+        h.sync()
+        phi, cnt = h.phi(), h.counters()
+        h.close()
+        ref = oracle.run(m, c, w["seed"], 0, 64)
+        compare_phi(phi, ref, cnt, 1e-6)
+
+
 # ------------------------------------------------------------------ closed loop
 
 def compare_phi(dev_phi, ref, dev_cnt, tol):
