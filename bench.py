@@ -470,12 +470,16 @@ def main():
                 fdr[(kk, sgn)] = hf.phi()
                 okf &= hf.counters()["n_ocp_failed"] == 0
         hf.close()
-        fd_err = []
+        # per trajectory: Phi_j is piecewise smooth in the weights and a
+        # difference that straddles an active-set change is no derivative
+        fd_med, fd_frac = [], []
         for q, kk in enumerate(("Qz", "Ru", "Qn")):
             hk = 1e-2 * cf[kk]
-            fdm = float(((fdr[(kk, 1)] - fdr[(kk, -1)])[okf] / (2 * hk)).mean())
-            tgm = float(gf[okf, q].mean())
-            fd_err.append(abs(fdm / tgm - 1.0) if tgm != 0 else None)
+            fdj = (fdr[(kk, 1)] - fdr[(kk, -1)])[okf] / (2 * hk)
+            tj = gf[okf, q]
+            rel = np.abs(fdj - tj) / (np.abs(tj) + 1e-2 * np.abs(tj).max())
+            fd_med.append(float(np.median(rel)))
+            fd_frac.append(float(np.mean(rel <= 5e-2)))
         if world > 1:
             t = torch.tensor([ng_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -487,7 +491,8 @@ def main():
                  "grad_mean": ng_mean.tolist(),
                  "ocps_without_sensitivity": ng_st["qp_fail"],
                  "fd_check": {"trajectories": int(okf.sum()), "of": nf, "n_steps": 24,
-                              "sqp_tol": 1e-7, "h_rel": 1e-2, "rel_err": fd_err}}
+                              "sqp_tol": 1e-7, "h_rel": 1e-2, "median_rel_err": fd_med,
+                              "frac_within_5e-2": fd_frac}}
 
     # end to end through the C ABI with host buffers: create (config h2d),
     # run, stats and Phi copied back to host, destroy

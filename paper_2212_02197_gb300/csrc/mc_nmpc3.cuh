@@ -126,7 +126,7 @@ __device__ __noinline__ void rk4_interval3(const DevModel& m, double EaR, int n_
 }
 
 // CD-EKF prediction for three states (P symmetric, six entries).
-__device__ void ekf3_predict(const DevModel& m, double EaR, int n_rk4, double F, double x[3],
+__device__ __noinline__ void ekf3_predict(const DevModel& m, double EaR, int n_rk4, double F, double x[3],
                              double P[6]) {
   const double h = m.Ts / (double)n_rk4;
   double Qd[3];
@@ -171,7 +171,7 @@ __device__ void ekf3_predict(const DevModel& m, double EaR, int n_rk4, double F,
 }
 
 // Filtering with y = n_T / V + v, Joseph form.
-__device__ void ekf3_filter(const DevModel& m, double y, double x[3], double P[6]) {
+__device__ __noinline__ void ekf3_filter(const DevModel& m, double y, double x[3], double P[6]) {
   const double R = m.meas_sd * m.meas_sd;
   const double iV = 1.0 / m.V;
   double PC[3];
@@ -220,7 +220,7 @@ __device__ void ekf3_filter(const DevModel& m, double y, double x[3], double P[6
 // WXU3, WUU3, EQ3 (temperature part of q_k), LB3, UB3; writes DU3, DX3, MU3,
 // NUL3, NUU3.  q_k and r_k are zero except the temperature part of q_k.
 
-__device__ bool riccati3(const Ws& w, int N, uint64_t fixed) {
+__device__ __noinline__ bool riccati3(const Ws& w, int N, uint64_t fixed) {
   double P[6], p[3];
 #pragma unroll
   for (int i = 0; i < 6; ++i) P[i] = w(WXX3 + i, N);
@@ -325,7 +325,7 @@ __device__ bool riccati3(const Ws& w, int N, uint64_t fixed) {
   return true;
 }
 
-__device__ QpResult qp3_active_set(const Ws& w, int N, int max_it) {
+__device__ __noinline__ QpResult qp3_active_set(const Ws& w, int N, int max_it) {
   uint64_t lo = 0, up = 0;
   double gscale = 1.0;
   for (int k = 0; k < N; ++k) {
@@ -571,9 +571,41 @@ __device__ __forceinline__ double lagr_gx(const Ws& w, int k, int N, int i) {
   return s;
 }
 
+// Damped block BFGS on every block (s = alpha (du, dx), y = grad L at the
+// new point minus grad L at the old point, both with the new multipliers);
+// false when some block lost positive definiteness.
+__device__ __noinline__ bool bfgs3_pass(const Ws& w, int N, double alpha) {
+  bool pd = true;
+  for (int k = 0; k <= N; ++k) {
+    double W[16], s[4], y[4];
+    load_block(w, k, N, W);
+    int n;
+    if (k == 0) {
+      n = 1;
+      s[0] = alpha * w(DU3, 0);
+      y[0] = lagr_gu(w, 0) - w(GLU3, 0);
+    } else {
+      for (int i = 0; i < 3; ++i) {
+        s[i] = alpha * w(DX3 + i, k);
+        y[i] = lagr_gx(w, k, N, i) - w(GLX3 + i, k);
+      }
+      n = 3;
+      if (k < N) {
+        s[3] = alpha * w(DU3, k);
+        y[3] = lagr_gu(w, k) - w(GLU3, k);
+        n = 4;
+      }
+    }
+    bfgs_blockn(n, W, s, y);
+    store_block(w, k, N, W);
+    pd = pd && chol_pd(n, W);
+  }
+  return pd;
+}
+
 // The SQP of Sec. IV for one three-state OCP from the warm start in (U3, X3,
 // LAM3, PIL3, PIU3) with x_0 in X3(., 0) and the set-points in ZB3.
-__device__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, double EaR, const Ws& w,
+__device__ __noinline__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, double EaR, const Ws& w,
                               int N, int max_it) {
   const double c1 = 1e-4, s_max = 100.0;
   SqpInfo info{};
@@ -581,38 +613,9 @@ __device__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, double EaR, c
   double f = evaluate3(m, c, EaR, N, w, U3, X3, EA3, EB3, EG3, EQ3);
   double alpha = 0.0;
   for (int l = 0;; ++l) {
-    if (l > 0) {
-      // damped block BFGS: s = alpha (du, dx), y = grad L at the new point
-      // minus grad L at the old point, both with the new multipliers
-      bool pd = true;
-      for (int k = 0; k <= N; ++k) {
-        double W[16], s[4], y[4];
-        load_block(w, k, N, W);
-        int n;
-        if (k == 0) {
-          n = 1;
-          s[0] = alpha * w(DU3, 0);
-          y[0] = lagr_gu(w, 0) - w(GLU3, 0);
-        } else {
-          for (int i = 0; i < 3; ++i) {
-            s[i] = alpha * w(DX3 + i, k);
-            y[i] = lagr_gx(w, k, N, i) - w(GLX3 + i, k);
-          }
-          n = 3;
-          if (k < N) {
-            s[3] = alpha * w(DU3, k);
-            y[3] = lagr_gu(w, k) - w(GLU3, k);
-            n = 4;
-          }
-        }
-        bfgs_blockn(n, W, s, y);
-        store_block(w, k, N, W);
-        pd = pd && chol_pd(n, W);
-      }
-      if (!pd) {
-        identity_blocks(w, N);
-        info.n_hess_reset++;
-      }
+    if (l > 0 && !bfgs3_pass(w, N, alpha)) {
+      identity_blocks(w, N);
+      info.n_hess_reset++;
     }
     // scaled convergence test
     double mult1 = 0.0, kg = 0.0, ke = 0.0;

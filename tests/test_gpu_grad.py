@@ -230,14 +230,18 @@ def test_nmpc_grad_phi_equals_the_static_run():
     h.close()
 
 
-def test_nmpc_mean_gradient_matches_central_differences():
+def test_nmpc_gradient_matches_central_differences():
     """The tangent is the derivative of the closed loop whose OCPs sit exactly
-    at their KKT points.  An SQP stopped at a finite tolerance lags that map
-    (its input moves less than the solution would), so central differences of
-    the simulated Phi approach the tangent as the tolerance tightens: about
-    15 % apart at 1e-5, 10 % at 1e-6, a few percent at 1e-7 (measured with the
-    oracle).  Here: OCPs solved to 1e-7, steps of 1e-2 of each weight, means
-    over the trajectories whose OCPs all converged in every run."""
+    at their KKT points.  Phi_j is only piecewise smooth in the weights: where
+    an OCP along the trajectory changes its active set (an input bound) inside
+    [w - h, w + h], a central difference straddles the kink and says nothing
+    about the local derivative.  Those trajectories are few but their
+    differences are large, so they dominate a mean; the comparison is
+    therefore per trajectory: most trajectories agree to a small multiple of
+    the SQP tolerance's effect, and only a minority may straddle a kink
+    (with the oracle, median relative error 1e-5, 90th percentile 2e-3 for
+    Q_z and R_u).  OCPs solved to 1e-7, steps of 1e-2 of each weight,
+    trajectories whose OCPs all converged in every run."""
     w = W.get(WN)
     m = dict(w["model"], n_steps=24)
     c = dict(w["nmpc"], Ru=0.2, Qn=1.0, sqp_tol=1e-7, sqp_max_it=300, schedule="static")
@@ -263,7 +267,10 @@ def test_nmpc_mean_gradient_matches_central_differences():
     for q, k in enumerate(("Qz", "Ru", "Qn")):
         hk = 1e-2 * c[k]
         fd = (runs[(k, 1)][ok] - runs[(k, -1)][ok]) / (2 * hk)
-        assert fd.mean() == pytest.approx(g[ok, q].mean(), rel=5e-2), (k, fd.mean(), g[ok, q].mean())
+        t = g[ok, q]
+        rel = np.abs(fd - t) / (np.abs(t) + 1e-2 * np.abs(t).max())
+        assert np.median(rel) <= 1e-3, (k, np.median(rel))
+        assert np.mean(rel <= 5e-2) >= 0.85, (k, np.mean(rel <= 5e-2))
 
 
 def test_nmpc_autograd_and_errors():
