@@ -44,14 +44,14 @@ DEFAULT_WORKLOAD = "cstr_30k_x240_N20_fp64"
 # equivalents by a throughput micro-benchmark (see the design notes).
 W_EXP, W_DIV, W_LOG, W_SQRT, W_SINCOS = 16.9, 5.6, 29.3, 8.6, 26.7
 # per unit, from the kernel source (one state, one input):
-OPS_MODEL1 = 24 + W_EXP + W_DIV               # f, df/dx, df/dF of the one-state model
-OPS_RK4_SENS = 4 * OPS_MODEL1 + 33            # one RK4 step with forward sensitivities
-OPS_INTERVAL_EXTRA = 8                        # g_k, q_k, objective term
+OPS_MODEL1 = 15 + W_EXP + W_DIV               # f, df/dx, df/dF of the one-state model
+OPS_RK4_SENS = 4 * OPS_MODEL1 + 29            # one RK4 step with forward sensitivities
+OPS_INTERVAL_EXTRA = 10                       # F/V, B = Fconv b, g_k, q_k, objective term
 OPS_QP_STAGE = 24 + W_DIV                     # active-set iteration, per stage
 OPS_SQP_STAGE = 45 + 2 * W_DIV                # gradient, KKT test, block BFGS, merit
 OPS_ACCEPT_STAGE = 15 + W_DIV                 # multiplier step, gradients, copy
 OPS_TRIAL_STAGE = 6                           # trial point and its merit sum
-OPS_EKF = 5 * (4 * (20 + W_EXP + W_DIV) + 12) + 12 + W_DIV   # predict (N_c = 5) + filter
+OPS_EKF = 5 * (4 * (19 + W_EXP + W_DIV) + 8) + 12 + W_DIV    # predict (N_c = 5) + filter
 OPS_EM = 38 + W_EXP + W_DIV - 5.6 + 12 + 2 * (8 + W_LOG + W_SQRT + W_SINCOS)  # substep
 PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
 

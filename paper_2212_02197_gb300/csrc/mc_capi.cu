@@ -581,6 +581,10 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   m->Ea_logsd = mm->Ea_logsd; m->dTin = mm->dT_in_step;
   m->Ea_plant_only = mm->Ea_plant_only;
   m->iV = 1.0 / mm->V; m->ib = 1.0 / mm->beta;
+  m->rw0 = m->ib * (mm->cB_in + 2.0 * mm->cA_in);
+  m->rw1 = 4.0 * m->ib * m->ib;
+  m->bV = mm->beta * mm->V;
+  m->ib2 = 2.0 * m->ib;
   m->key0 = (uint32_t)seed; m->key1 = (uint32_t)(seed >> 32);
   memset(c, 0, sizeof(*c));
   c->kind = cc->kind; c->precision = cc->precision; c->N = cc->N; c->n_rk4 = cc->n_rk4;

@@ -31,6 +31,8 @@ struct DevModel {
   double sp_time[kMaxSp], sp_value[kMaxSp];
   double Ea_logsd, dTin;
   double iV, ib;       // 1/V and 1/beta
+  double rw0, rw1, bV, ib2;  // one-state rate law: ib (cB_in + 2 cA_in), 4 ib^2,
+                            // beta V, 2 ib
   uint32_t key0, key1;
 };
 
@@ -229,27 +231,38 @@ __device__ __forceinline__ void em_step(const DevModel& m, R EaR, R T_in, R n[3]
 }
 
 // One-state model (Sec. VI) in x = n_T; c_A, c_B from the reaction invariants.
-// Returns f and df/dx, df/dF.
+// Returns f and df/dx, df/dF.  With c_T = x / V, d = T_in - c_T, the invariants
+// give c_A = c_A,in + d / beta and c_B = c_B,in + 2 d / beta, and
+//   r = k(c_T) c_A c_B,  k = k_0 exp(-g),  g = (E_a/R) / c_T,
+//   f = F d + beta V r,
+//   dr/dc_T = r g / c_T - k (c_B + 2 c_A) / beta,
+//   df/dx = -F / V + beta dr/dc_T,
+// where (c_B + 2 c_A) / beta = rw0 + rw1 d is affine in d.  Written this way
+// the evaluation takes 15 FP64 operations besides the exp and the reciprocal
+// (and one, F / V, that stays the same over an interval).
 template <class R>
 __device__ __forceinline__ void model1(const DevModel& m, R EaR, R x, R F, R& f, R& fx,
                                        R& fF) {
-  const R V = (R)m.V, beta = (R)m.beta, Tin = (R)m.T_in;
   const R iV = (R)m.iV, ib = (R)m.ib;
   const R cT = x * iV;
-  const R cA = (R)m.cA_in + (Tin - cT) * ib;
-  const R cB = (R)m.cB_in + (R)2 * (Tin - cT) * ib;
+  const R d = (R)m.T_in - cT;
   const R iT = (R)1 / cT;
-  const R k = (R)m.k0 * expr(-EaR * iT);
-  const R r = k * cA * cB;
-  f = F * (Tin - cT) + beta * r * V;
-  const R dk = k * EaR * iT * iT;
-  const R dr = dk * cA * cB - k * ib * cB - (R)2 * k * ib * cA;
-  fx = (-F + beta * dr * V) * iV;
-  fF = Tin - cT;
+  const R g = EaR * iT;
+  const R k = (R)m.k0 * expr(-g);
+  const R cA = fma(d, ib, (R)m.cA_in);
+  const R cB = fma(d, (R)m.ib2, (R)m.cB_in);
+  const R r = k * (cA * cB);
+  f = fma((R)m.bV, r, F * d);
+  const R ibw = fma((R)m.rw1, d, (R)m.rw0);
+  const R dr = fma(r, g * iT, -(k * ibw));
+  fx = fma((R)m.beta, dr, -(F * iV));
+  fF = d;
 }
 
 // One shooting interval: n_rk4 classical RK4 steps over Ts from x0 (K L) with
-// flow F = v Fconv, and the forward sensitivities a = dx/dx0, b = dx/dv.
+// flow F = v Fconv, and the forward sensitivities a = dx/dx0, B = dx/dv.
+// The RK4 stages propagate b = dx/dF, whose forcing is df/dF itself; B is
+// Fconv b, formed once at the end.
 template <class R, bool kSens>
 __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4, R Ts, R x0,
                                              R v, R Fconv, R& xF, R& A, R& B) {
@@ -267,10 +280,10 @@ __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4
     const R x4 = x + h * f3;
     model1<R>(m, EaR, x4, F, f4, fx4, fF4);
     if (kSens) {
-      const R a1 = fx1 * a, b1 = fx1 * b + fF1 * Fconv;
-      const R a2 = fx2 * (a + hh * a1), b2 = fx2 * (b + hh * b1) + fF2 * Fconv;
-      const R a3 = fx3 * (a + hh * a2), b3 = fx3 * (b + hh * b2) + fF3 * Fconv;
-      const R a4 = fx4 * (a + h * a3), b4 = fx4 * (b + h * b3) + fF4 * Fconv;
+      const R a1 = fx1 * a, b1 = fma(fx1, b, fF1);
+      const R a2 = fx2 * fma(hh, a1, a), b2 = fma(fx2, fma(hh, b1, b), fF2);
+      const R a3 = fx3 * fma(hh, a2, a), b3 = fma(fx3, fma(hh, b2, b), fF3);
+      const R a4 = fx4 * fma(h, a3, a), b4 = fma(fx4, fma(h, b3, b), fF4);
       a = a + h6 * (a1 + (R)2 * a2 + (R)2 * a3 + a4);
       b = b + h6 * (b1 + (R)2 * b2 + (R)2 * b3 + b4);
     }
@@ -278,7 +291,7 @@ __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4
   }
   xF = x;
   A = a;
-  B = b;
+  B = kSens ? b * Fconv : b;
 }
 
 // CD-EKF prediction, Eq. (predictionEquations): RK4 on (x, P) with
