@@ -6,12 +6,12 @@
 //   traj_nmpc        one trajectory per thread, SQPs run to completion one after
 //                    the other; the lanes of a warp wait for the slowest OCP
 //   nmpc_persistent  a per-lane state machine: every lane advances its own
-//                    trajectory through the cheap phases until it needs a
-//                    line-search evaluation, and the warp then shoots all
-//                    pending trial points together (or, when few are
-//                    pending, each in turn with its intervals spread over the
-//                    lanes); finished lanes take the next trajectory from a
-//                    queue.  Same arithmetic per trajectory, bit for bit.
+//                    trajectory through the cheap phases until it needs
+//                    shooting (a line-search trial point, or the first
+//                    evaluation of a new OCP), and the warp then shoots all
+//                    pending intervals as one pool spread over its lanes;
+//                    finished lanes take the next trajectory from a queue.
+//                    Same arithmetic per trajectory, bit for bit.
 #pragma once
 
 #include "mc_sqp.cuh"
@@ -118,7 +118,8 @@ __device__ __forceinline__ void nmpc_begin(const DevModel& m, const DevCtrl& c, 
 // finished (T.out is final).
 template <class R>
 __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtrl& c,
-                                                 const Ws& w, NmpcTraj& T, SqpState& s) {
+                                                 const Ws& w, NmpcTraj& T, SqpState& s,
+                                                 bool shoot) {
   const int K = m.n_steps, N = T.tp.N;
   const double t_i = m.t0 + (double)T.i * m.Ts;
   const double cT = T.n[2] / m.V;
@@ -144,7 +145,8 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
   for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(T.i + k) * m.Ts);
   if (c.Ru != 0.0)
     for (int k = 1; k <= N; ++k) w(VB, k) = Fss(m, T.tp.EaR_c, w(ZB, k)) / c.Fconv;
-  sqp_start<R>(m, c, T.tp.EaR_c, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s);
+  sqp_start<R>(m, c, T.tp.EaR_c, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s,
+               shoot);
   return true;
 }
 
@@ -180,19 +182,21 @@ __device__ __forceinline__ void nmpc_apply_body(const DevModel& m, const DevCtrl
 // Code placement as for sqp_check: separate functions on the mixed path.
 template <class R>
 __device__ __noinline__ bool nmpc_sample_call(const DevModel& m, const DevCtrl& c, const Ws& w,
-                                              NmpcTraj& T, SqpState& s) {
-  return nmpc_sample_body<R>(m, c, w, T, s);
+                                              NmpcTraj& T, SqpState& s, bool shoot) {
+  return nmpc_sample_body<R>(m, c, w, T, s, shoot);
 }
 template <class R>
 __device__ __noinline__ void nmpc_apply_call(const DevModel& m, const DevCtrl& c, const Ws& w,
                                              NmpcTraj& T, const SqpInfo& si) {
   nmpc_apply_body<R>(m, c, w, T, si);
 }
+// shoot = false: the OCP's first evaluation is left to the caller (the
+// persistent schedule's pool, then sqp_start_eval).
 template <class R>
 __device__ __forceinline__ bool nmpc_sample(const DevModel& m, const DevCtrl& c, const Ws& w,
-                                            NmpcTraj& T, SqpState& s) {
-  if constexpr (sizeof(R) == 4) return nmpc_sample_call<R>(m, c, w, T, s);
-  else return nmpc_sample_body<R>(m, c, w, T, s);
+                                            NmpcTraj& T, SqpState& s, bool shoot = true) {
+  if constexpr (sizeof(R) == 4) return nmpc_sample_call<R>(m, c, w, T, s, shoot);
+  else return nmpc_sample_body<R>(m, c, w, T, s, shoot);
 }
 template <class R>
 __device__ __forceinline__ void nmpc_apply(const DevModel& m, const DevCtrl& c, const Ws& w,
@@ -224,23 +228,99 @@ __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, co
   return T.out;
 }
 
-// Persistent schedule.  Every lane of the warp must call this (it uses warp
-// votes); trajectories come from the queue `next` (positions 0 .. n-1, mapped
-// through `order` when given, else to j0 + position) and are written to
-// phi_out / cnt_out.
-enum LanePhase : int { kNewTraj = 0, kSample = 1, kCheck = 2, kTrial = 3, kDone = 4 };
+// ---------------------------------------------------------------------------
+// Persistent schedule: the shooting pool.
+//
+// Every shooting interval the warp needs in a round -- the N_o intervals of
+// each pending trial point, and the intervals 0 and N-1 (all N on the first
+// sample) of each OCP that just started -- is one job.  The jobs are numbered
+// interval-major (job position i of every lane that has one, lanes in order,
+// then position i + 1) and lane t takes jobs t, t + 32, ...; so a round with
+// every lane pending shoots like the joint loop (lane t integrates its own
+// interval i, coalesced), and a round with few pending lanes spreads their
+// intervals over the whole warp.  Each job is one call of the shoot_interval
+// body, whichever lane runs it: the results are those of evaluate, bit for bit.
+
+enum PoolMode : int { kPoolTrial = 0, kPoolStartEnds = 1, kPoolStartAll = 2 };
+
+struct PoolTab {
+  unsigned mask[MC_MAX_HORIZON];  // lanes with a job at position i
+  int pref[MC_MAX_HORIZON];       // jobs before position i
+  double EaR[32];
+  int N[32], mode[32];
+};
+
+template <class R>
+__device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                           int n_jobs, int mode, int N, double EaR,
+                                           PoolTab& tab) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int max_jobs = (int)__reduce_max_sync(full, (unsigned)n_jobs);
+  __syncwarp();  // the previous round's readers of tab are done
+  tab.EaR[lane] = EaR;
+  tab.N[lane] = N;
+  tab.mode[lane] = mode;
+  int total = 0;
+  for (int i = 0; i < max_jobs; ++i) {
+    const unsigned mi = __ballot_sync(full, n_jobs > i);
+    if (lane == 0) {
+      tab.mask[i] = mi;
+      tab.pref[i] = total;
+    }
+    total += __popc(mi);
+  }
+  __syncwarp();  // tab and the owners' points are visible to every lane
+  const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
+  for (int q = lane; q < total; q += 32) {
+    int lo = 0, hi = max_jobs;  // pref[lo] <= q < pref[hi], pref[max_jobs] = total
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tab.pref[mid] <= q) lo = mid;
+      else hi = mid;
+    }
+    unsigned mo = tab.mask[lo];
+    for (int r = q - tab.pref[lo]; r > 0; --r) mo &= mo - 1u;
+    const int o = __ffs(mo) - 1;
+    const int md = tab.mode[o];
+    const int k = (md == kPoolStartEnds && lo == 1) ? tab.N[o] - 1 : lo;
+    const bool trial = (md == kPoolTrial);
+    const int ua = trial ? UT : U, xa = trial ? XT : X;
+    const int aa = trial ? TA : EA, ba = trial ? TB : EB, ga = trial ? TG : EG;
+    const Ws wo{w.p + (o - lane), w.ld, w.N1};
+    const double xk = (k == 0) ? wo(X, 0) : wo(xa, k);
+    double A, B, g;
+    shoot_interval<R>(m, c, tab.EaR[o], xk, wo(ua, k), wo(xa, k + 1), xs, ixs, A, B, g);
+    wo(aa, k) = A;
+    wo(ba, k) = B;
+    wo(ga, k) = g;
+  }
+  __syncwarp();  // the shot intervals are visible to their owners
+}
+
+// Every lane of the warp must call this (it uses warp votes); trajectories
+// come from the queue `next` (positions 0 .. n-1, mapped through `order` when
+// given, else to j0 + position) and are written to phi_out / cnt_out.
+//
+// A round: each lane runs its cheap phases until it needs shooting -- a trial
+// point (kTrial), or the first evaluation of the OCP it just started (kStart)
+// -- then the warp shoots all of it in the pool, and each lane finishes its
+// evaluation.  A started OCP takes its first QP in the next round's check,
+// together with the other lanes' checks, rather than on its own.
+enum LanePhase : int { kNewTraj = 0, kSample = 1, kCheck = 2, kTrial = 3, kStart = 4, kDone = 5 };
 
 template <class R>
 __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w, int64_t j0,
                                 int64_t n, const uint32_t* __restrict__ order,
                                 unsigned long long* next, double* __restrict__ phi_out,
                                 int32_t* __restrict__ cnt_out) {
+  __shared__ PoolTab tab;  // one per block: the kernel runs one warp per block
   NmpcTraj T;
   SqpState s;
   int phase = kNewTraj;
   for (;;) {
-    // cheap, divergent phases until this lane needs a trial evaluation
-    while (phase != kTrial && phase != kDone) {
+    // cheap, divergent phases until this lane needs shooting
+    while (phase != kTrial && phase != kStart && phase != kDone) {
       if (phase == kNewTraj) {
         const unsigned long long q = atomicAdd(next, 1ull);
         if (q >= (unsigned long long)n) {
@@ -252,16 +332,16 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
         phase = kSample;
       }
       if (phase == kSample) {
-        if (nmpc_sample<R>(m, c, w, T, s)) {
-          phase = kCheck;
+        if (nmpc_sample<R>(m, c, w, T, s, false)) {
+          phase = kStart;
         } else {
           phi_out[T.j] = T.out.phi;
 #pragma unroll
           for (int q = 0; q < kNCounters; ++q)
             cnt_out[(int64_t)T.j * kNCounters + q] = T.out.cnt[q];
           phase = kNewTraj;
-          continue;
         }
+        continue;
       }
       if (phase == kCheck) {
         if (sqp_check<R>(c, w, s)) {
@@ -272,34 +352,21 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
         }
       }
     }
-    // the shared, expensive part: all lanes with a pending trial shoot it
-    const unsigned tm = __ballot_sync(0xffffffffu, phase == kTrial);
-    if (!tm) break;
-    // Jointly, the warp runs the longest pending horizon once; a warp
-    // instruction costs the FP64 pipe the same whatever its active lanes.
-    // Cooperatively, each pending trial is shot in turn with its intervals
-    // spread over the 32 lanes, at ceil(N/32) intervals per lane.  Few
-    // pending trials (the tail of a warp whose other lanes have finished)
-    // take the cooperative route.
-    const int Nt = (phase == kTrial) ? s.N : 0;
-    const unsigned maxN = __reduce_max_sync(0xffffffffu, (unsigned)Nt);
-    const unsigned coop = __reduce_add_sync(0xffffffffu, (unsigned)((Nt + 31) / 32));
-    if (8u * coop <= 7u * maxN) {
-      const int lane = threadIdx.x & 31;
-      __syncwarp();  // the owners' trial points are visible to the helpers
-      for (unsigned rem = tm; rem; rem &= rem - 1u) {
-        const int o = __ffs(rem) - 1;
-        const int No = __shfl_sync(0xffffffffu, s.N, o);
-        const double EaRo = __shfl_sync(0xffffffffu, T.tp.EaR_c, o);
-        const Ws wo{w.p + (o - lane), w.ld, w.N1};
-        sqp_shoot_trial_coop<R>(m, c, EaRo, No, wo, lane);
-      }
-      __syncwarp();  // the helpers' A_k, B_k, g_k are visible to the owners
-      if (phase == kTrial) sqp_eval_trial_shot<R>(m, c, T.tp.EaR_c, w, s);
-    } else if (phase == kTrial) {
-      sqp_eval_trial<R>(m, c, T.tp.EaR_c, w, s);
-    }
+    if (!__ballot_sync(0xffffffffu, phase != kDone)) break;
+    int n_jobs = 0, mode = kPoolTrial;
     if (phase == kTrial) {
+      n_jobs = s.N;
+    } else if (phase == kStart) {
+      const bool ends = (T.i > 0);
+      mode = ends ? kPoolStartEnds : kPoolStartAll;
+      n_jobs = ends ? (s.N > 1 ? 2 : 1) : s.N;
+    }
+    pool_shoot<R>(m, c, w, n_jobs, mode, s.N, T.tp.EaR_c, tab);
+    if (phase == kStart) {
+      sqp_start_eval<R>(m, c, T.tp.EaR_c, w, s);
+      phase = kCheck;
+    } else if (phase == kTrial) {
+      sqp_eval_trial_shot<R>(m, c, T.tp.EaR_c, w, s);
       const int r = sqp_trial_result<R>(c, w, s);
       if (r == 0) {
         phase = kCheck;

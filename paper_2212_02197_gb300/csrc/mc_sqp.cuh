@@ -37,9 +37,9 @@ struct SqpState {
 
 // One shooting interval with sensitivities: F_k = RK4^{N_c}(x_k, u_k) and
 // A_k = dF_k/dx_k, B_k = dF_k/du_k in the scaled variables, and the residual
-// g_k = F_k - x_{k+1}.  Not inlined: the joint loop of evaluate and the
-// cooperative shooting (one interval per lane) run this one compiled body, so
-// both give the same bits.
+// g_k = F_k - x_{k+1}.  Not inlined: the loop of evaluate and the persistent
+// schedule's shooting pool (any lane integrating any lane's interval) run this
+// one compiled body, so both give the same bits.
 template <class R>
 __device__ __noinline__ void shoot_interval(const DevModel& m, const DevCtrl& c, double EaR,
                                             double xk, double uk, double xn, double xs,
@@ -58,7 +58,7 @@ enum RkMode : int {
   kRkEnds = 1,  // only 0 and N-1: after the receding-horizon shift the
                 // intervals 1 .. N-2 hold the previous OCP's A_k, B_k, g_k at
                 // the same (x_k, u_k)
-  kRkNone = 2   // none: the arrays were filled by the cooperative shooting
+  kRkNone = 2   // none: the arrays were filled by the shooting pool
 };
 
 // Shooting of the intervals selected by rk_mode at the point (u_arr, x_arr),
@@ -149,10 +149,13 @@ __device__ __forceinline__ void sqp_trial_point(const DevCtrl& c, const Ws& w,
 // set-points z-bar(t_{i+k}) in ZB[1..N]; W^[0] = I.  With shifted_eval the
 // evaluation arrays hold the previous OCP's final evaluation shifted by one
 // interval (see evaluate).
+// With shoot = false the first evaluation is left to the caller: the
+// persistent schedule shoots the intervals kRkEnds or kRkAll names in its pool
+// and then calls sqp_start_eval.
 template <class R>
 __device__ __forceinline__ void sqp_start(const DevModel& m, const DevCtrl& c, double EaR,
                                           double x0, const Ws& w, int N, int max_it,
-                                          bool shifted_eval, SqpState& s) {
+                                          bool shifted_eval, SqpState& s, bool shoot = true) {
   s.N = N;
   s.max_it = max_it;
   s.l = 0;
@@ -165,7 +168,16 @@ __device__ __forceinline__ void sqp_start(const DevModel& m, const DevCtrl& c, d
     w(WUU, k) = 1.0;
   }
   w(X, 0) = x0;
-  s.f = evaluate<R>(m, c, EaR, N, w, U, X, EA, EB, EG, EQ, shifted_eval ? kRkEnds : kRkAll);
+  s.f = shoot ? evaluate<R>(m, c, EaR, N, w, U, X, EA, EB, EG, EQ,
+                            shifted_eval ? kRkEnds : kRkAll)
+              : 0.0;
+}
+
+// The first evaluation after its intervals were shot elsewhere.
+template <class R>
+__device__ __forceinline__ void sqp_start_eval(const DevModel& m, const DevCtrl& c, double EaR,
+                                               const Ws& w, SqpState& s) {
+  s.f = evaluate<R>(m, c, EaR, s.N, w, U, X, EA, EB, EG, EQ, kRkNone);
 }
 
 // Top of an SQP iteration at xi^[l] (evaluated): damped block BFGS for l > 0,
@@ -289,33 +301,13 @@ __device__ __forceinline__ void sqp_eval_trial(const DevModel& m, const DevCtrl&
   s.info.ls_trials++;
 }
 
-// The same trial evaluation after the warp has shot the intervals
-// (sqp_shoot_trial_coop): only the objective and q_k are formed here.
+// The same trial evaluation after the warp has shot the intervals (the
+// persistent schedule's pool): only the objective and q_k are formed here.
 template <class R>
 __device__ __forceinline__ void sqp_eval_trial_shot(const DevModel& m, const DevCtrl& c,
                                                     double EaR, const Ws& w, SqpState& s) {
   s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ, kRkNone);
   s.info.ls_trials++;
-}
-
-// Cooperative shooting of one lane's trial point: every lane of the warp
-// calls this with the owner's column wo, horizon No and E_a/R, and integrates
-// the intervals k = lane, lane + 32, ... in parallel with the other lanes.
-// The writes go to the owner's arrays; the caller orders them before the
-// owner reads (__syncwarp).
-template <class R>
-__device__ __forceinline__ void sqp_shoot_trial_coop(const DevModel& m, const DevCtrl& c,
-                                                     double EaRo, int No, const Ws& wo,
-                                                     int lane) {
-  const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
-  for (int k = lane; k < No; k += 32) {
-    const double xk = (k == 0) ? wo(X, 0) : wo(XT, k);
-    double A, B, g;
-    shoot_interval<R>(m, c, EaRo, xk, wo(UT, k), wo(XT, k + 1), xs, ixs, A, B, g);
-    wo(TA, k) = A;
-    wo(TB, k) = B;
-    wo(TG, k) = g;
-  }
 }
 
 // Armijo test of the evaluated trial point.  Returns 0 when the step was
