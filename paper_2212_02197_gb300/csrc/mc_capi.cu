@@ -89,12 +89,13 @@ __global__ void __launch_bounds__(32) k_nmpc_persist(DevModel m, DevCtrl c, int6
                                                      unsigned long long* next,
                                                      double* __restrict__ phi,
                                                      int32_t* __restrict__ cnt, double* ws,
-                                                     int64_t ld) {
+                                                     int64_t ld, double* nz) {
   // launched with whole warps and at most ld threads; every lane takes part in
-  // the warp votes of nmpc_persistent
+  // the warp votes of nmpc_persistent.  nz: 3 n_em rows of ld columns, the
+  // pooled plant noise.
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Ws w{ws + t, ld, c.N + 1};
-  nmpc_persistent<R>(m, c, w, j0, n, order, next, phi, cnt);
+  nmpc_persistent<R>(m, c, w, nz + t, j0, n, order, next, phi, cnt);
 }
 
 template <class R>
@@ -463,6 +464,7 @@ struct mc_handle {
   double* phi = nullptr;       // n_sims
   int32_t* cnt = nullptr;      // n_sims x kNCounters
   double* ws = nullptr;        // NMPC scratch: kNArr * (N+1) x ws_ld
+  double* nz = nullptr;        // inside ws: 3 n_em x ws_ld plant normals (one-state)
   int64_t ws_ld = 0;
   int schedule = MC_SCHED_STATIC;
   uint32_t* order = nullptr;   // trajectories, longest horizon first (uneven batches)
@@ -699,10 +701,14 @@ mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl, int64_
             alloc((void**)&h->dstats, sizeof(DevStats));
   if (ok && h->c.kind == MC_CTRL_NMPC && n_sims > 0) {
     h->ws_ld = nmpc_threads_for(n_sims, h->c.nx_model);
-    const size_t words =
+    // the one-state path adds the persistent schedule's plant noise rows
+    const size_t main_words =
         (size_t)(h->c.nx_model == 3 ? (int)kNArr3 : (int)kNArr) * (h->c.N + 1) * (size_t)h->ws_ld;
+    const size_t words =
+        main_words + (h->c.nx_model == 3 ? 0 : (size_t)3 * h->m.n_em * (size_t)h->ws_ld);
     ok = alloc((void**)&h->ws, words * sizeof(double)) &&
          alloc((void**)&h->next, sizeof(unsigned long long));
+    if (ok) h->nz = h->ws + main_words;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -785,11 +791,11 @@ static mc_status enqueue_run(mc_handle* h, const DevModel& m, int64_t j0, int64_
       MC_CUDA(h, cudaMemsetAsync(h->next, 0, sizeof(unsigned long long), st));
       const unsigned blocks = (unsigned)(threads / kNmpcThreads);
       if (h->c.precision == MC_FP64)
-        k_nmpc_persist<double><<<blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, n, order, h->next,
-                                                               h->phi, h->cnt, h->ws, h->ws_ld);
+        k_nmpc_persist<double><<<blocks, kNmpcThreads, 0, st>>>(
+            m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz);
       else
-        k_nmpc_persist<float><<<blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, n, order, h->next,
-                                                              h->phi, h->cnt, h->ws, h->ws_ld);
+        k_nmpc_persist<float><<<blocks, kNmpcThreads, 0, st>>>(
+            m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz);
     } else if (h->c.kind == MC_CTRL_NMPC) {
       const int64_t n = j1 - j0;
       int64_t threads = n < h->ws_ld ? n : h->ws_ld;

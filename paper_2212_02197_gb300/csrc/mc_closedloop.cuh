@@ -25,10 +25,14 @@ struct TrajOut {
 };
 
 // Plant between two samples: N_s Euler-Maruyama substeps with zero-order hold
-// on the flow F (L/s) and the inlet temperature (which steps at t_d).
+// on the flow F (L/s) and the inlet temperature (which steps at t_d).  The
+// substeps' normals are drawn here, or read from nzc (substep s, component d
+// at nzc[(3 s + d) nz_ld]) where the persistent schedule's pool drew them.
 template <class R>
 __device__ __forceinline__ void plant_interval(const DevModel& m, const TrajParams& tp,
-                                               uint32_t j, int i, double F, double n[3]) {
+                                               uint32_t j, int i, double F, double n[3],
+                                               const double* nzc = nullptr,
+                                               int64_t nz_ld = 0) {
   const double h = m.Ts / (double)m.n_em;
   const R hR = (R)h, sqh = (R)sqrt(h);
   R nr[3] = {(R)n[0], (R)n[1], (R)n[2]};
@@ -38,7 +42,12 @@ __device__ __forceinline__ void plant_interval(const DevModel& m, const TrajPara
     const double tau = m.t0 + (double)ks * h;
     const double Tin = (m.dTin != 0.0 && tau >= tp.t_d) ? m.T_in + tp.dTin : m.T_in;
     R xi[3];
-    process_noise<R>(m, j, (uint32_t)ks, xi);
+    if (nzc) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) xi[d] = (R)nzc[(3 * s + d) * nz_ld];
+    } else {
+      process_noise<R>(m, j, (uint32_t)ks, xi);
+    }
     em_step<R>(m, EaR, (R)Tin, nr, FR, hR, sqh, xi);
   }
   n[0] = (double)nr[0];
@@ -154,7 +163,8 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
 // the final evaluation) one interval, simulate the plant to t_{i+1}.
 template <class R>
 __device__ __forceinline__ void nmpc_apply_body(const DevModel& m, const DevCtrl& c,
-                                                const Ws& w, NmpcTraj& T, const SqpInfo& si) {
+                                                const Ws& w, NmpcTraj& T, const SqpInfo& si,
+                                                const double* nzc, int64_t nz_ld) {
   const int N = T.tp.N;
   T.out.cnt[0] += (si.status == 1);
   T.out.cnt[1] += si.iters;
@@ -174,7 +184,7 @@ __device__ __forceinline__ void nmpc_apply_body(const DevModel& m, const DevCtrl
     w(EB, k) = w(EB, k + 1);
     w(EG, k) = w(EG, k + 1);
   }
-  plant_interval<R>(m, T.tp, T.j, T.i, F, T.n);
+  plant_interval<R>(m, T.tp, T.j, T.i, F, T.n, nzc, nz_ld);
   T.F_prev = F;
   T.i++;
 }
@@ -187,8 +197,9 @@ __device__ __noinline__ bool nmpc_sample_call(const DevModel& m, const DevCtrl& 
 }
 template <class R>
 __device__ __noinline__ void nmpc_apply_call(const DevModel& m, const DevCtrl& c, const Ws& w,
-                                             NmpcTraj& T, const SqpInfo& si) {
-  nmpc_apply_body<R>(m, c, w, T, si);
+                                             NmpcTraj& T, const SqpInfo& si,
+                                             const double* nzc, int64_t nz_ld) {
+  nmpc_apply_body<R>(m, c, w, T, si, nzc, nz_ld);
 }
 // shoot = false: the OCP's first evaluation is left to the caller (the
 // persistent schedule's pool, then sqp_start_eval).
@@ -198,11 +209,13 @@ __device__ __forceinline__ bool nmpc_sample(const DevModel& m, const DevCtrl& c,
   if constexpr (sizeof(R) == 4) return nmpc_sample_call<R>(m, c, w, T, s, shoot);
   else return nmpc_sample_body<R>(m, c, w, T, s, shoot);
 }
+// nzc: the plant interval's normals, drawn beforehand (see plant_interval).
 template <class R>
 __device__ __forceinline__ void nmpc_apply(const DevModel& m, const DevCtrl& c, const Ws& w,
-                                           NmpcTraj& T, const SqpInfo& si) {
-  if constexpr (sizeof(R) == 4) nmpc_apply_call<R>(m, c, w, T, si);
-  else nmpc_apply_body<R>(m, c, w, T, si);
+                                           NmpcTraj& T, const SqpInfo& si,
+                                           const double* nzc = nullptr, int64_t nz_ld = 0) {
+  if constexpr (sizeof(R) == 4) nmpc_apply_call<R>(m, c, w, T, si, nzc, nz_ld);
+  else nmpc_apply_body<R>(m, c, w, T, si, nzc, nz_ld);
 }
 
 // R = double: the FP64 path.  R = float: the mixed-precision path -- plant
@@ -248,6 +261,8 @@ struct PoolTab {
   int pref[MC_MAX_HORIZON];       // jobs before position i
   double EaR[32];
   int N[32], mode[32];
+  uint32_t j[32];                 // trajectory and sample of each lane's OCP
+  int i[32];
 };
 
 template <class R>
@@ -298,6 +313,49 @@ __device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, 
   __syncwarp();  // the shot intervals are visible to their owners
 }
 
+// One Box-Muller pair of process noise (counter (ks, j, tag, 0)); not inlined,
+// so that the elementary functions do not add to the schedule's registers.
+template <class R>
+__device__ __noinline__ double2 pool_normal_pair(const DevModel& m, uint32_t ks, uint32_t j,
+                                                 uint32_t tag) {
+  return Normal2<R>::from(philox4x32_10(make_uint4(ks, j, tag, 0u), m.key0, m.key1));
+}
+
+// The normals of the plant interval that follows each OCP started this round
+// (2 N_s Box-Muller pairs per lane: tags 0 and 1 of each substep, Philox
+// counters as in process_noise), drawn by the whole warp, substep-major, into
+// the owners' columns of nz (substep s, component d at nz[(3 s + d) ld]).
+template <class R>
+__device__ __forceinline__ void pool_noise(const DevModel& m, double* nzl, int64_t ld,
+                                           bool starting, uint32_t j, int i, PoolTab& tab) {
+  const unsigned sm = __ballot_sync(0xffffffffu, starting);
+  if (!sm) return;
+  const int lane = threadIdx.x & 31;
+  tab.j[lane] = j;
+  tab.i[lane] = i;
+  __syncwarp();
+  const int P = __popc(sm);
+  const int total = P * 2 * m.n_em;
+  for (int q = lane; q < total; q += 32) {
+    const int e = q / P;
+    unsigned mo = sm;
+    for (int r = q - e * P; r > 0; --r) mo &= mo - 1u;
+    const int o = __ffs(mo) - 1;
+    const int sub = e >> 1;
+    const uint32_t tag = (uint32_t)(e & 1);
+    const uint32_t ks = (uint32_t)((int64_t)tab.i[o] * m.n_em + sub);
+    const double2 z = pool_normal_pair<R>(m, ks, tab.j[o], tag);
+    double* no = nzl + (o - lane);
+    if (tag == 0) {
+      no[(3 * sub) * ld] = (double)(R)z.x;
+      no[(3 * sub + 1) * ld] = (double)(R)z.y;
+    } else {
+      no[(3 * sub + 2) * ld] = (double)(R)z.x;
+    }
+  }
+  __syncwarp();
+}
+
 // Every lane of the warp must call this (it uses warp votes); trajectories
 // come from the queue `next` (positions 0 .. n-1, mapped through `order` when
 // given, else to j0 + position) and are written to phi_out / cnt_out.
@@ -310,8 +368,8 @@ __device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, 
 enum LanePhase : int { kNewTraj = 0, kSample = 1, kCheck = 2, kTrial = 3, kStart = 4, kDone = 5 };
 
 template <class R>
-__device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w, int64_t j0,
-                                int64_t n, const uint32_t* __restrict__ order,
+__device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w, double* nzl,
+                                int64_t j0, int64_t n, const uint32_t* __restrict__ order,
                                 unsigned long long* next, double* __restrict__ phi_out,
                                 int32_t* __restrict__ cnt_out) {
   __shared__ PoolTab tab;  // one per block: the kernel runs one warp per block
@@ -345,7 +403,7 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       }
       if (phase == kCheck) {
         if (sqp_check<R>(c, w, s)) {
-          nmpc_apply<R>(m, c, w, T, s.info);
+          nmpc_apply<R>(m, c, w, T, s.info, nzl, w.ld);
           phase = kSample;
         } else {
           phase = kTrial;
@@ -353,6 +411,7 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       }
     }
     if (!__ballot_sync(0xffffffffu, phase != kDone)) break;
+    pool_noise<R>(m, nzl, w.ld, phase == kStart, T.j, T.i, tab);
     int n_jobs = 0, mode = kPoolTrial;
     if (phase == kTrial) {
       n_jobs = s.N;
@@ -371,7 +430,7 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       if (r == 0) {
         phase = kCheck;
       } else if (r == 1) {
-        nmpc_apply<R>(m, c, w, T, s.info);
+        nmpc_apply<R>(m, c, w, T, s.info, nzl, w.ld);
         phase = kSample;
       }
     }
