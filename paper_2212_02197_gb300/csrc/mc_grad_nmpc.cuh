@@ -25,24 +25,30 @@ namespace mc {
 //   r' = k' c_A c_B + k (c_A' c_B + c_A c_B'),
 //   r'' = k'' c_A c_B + 2 k' (c_A' c_B + c_A c_B') + 2 k c_A' c_B',
 //   k' = k E / c_T^2, k'' = k E (E - 2 c_T) / c_T^4.
+// Evaluated with one reciprocal, as model1 does: with g = E / c_T and
+// i = 1 / c_T, k' = k g i and k'' = k g i^2 (g - 2); c_A' c_B + c_A c_B' =
+// -(c_B + 2 c_A) / beta = -(rw0 + rw1 d) for d = T_in - c_T; 2 c_A' c_B' = rw1.
 __device__ __forceinline__ void model1_d2(const DevModel& m, double EaR, double x, double F,
                                           double& f, double& fx, double& fF, double& fxx,
                                           double& fxF) {
-  const double V = m.V, beta = m.beta, Tin = m.T_in;
-  const double cT = x / V;
-  const double cA = m.cA_in + (Tin - cT) / beta, cB = m.cB_in + 2.0 * (Tin - cT) / beta;
-  const double dA = -1.0 / beta, dB = -2.0 / beta;
-  const double k = m.k0 * expr(-EaR / cT);
-  const double k1 = k * EaR / (cT * cT);
-  const double k2 = k * EaR * (EaR - 2.0 * cT) / (cT * cT * cT * cT);
-  const double r = k * cA * cB;
-  const double r1 = k1 * cA * cB + k * (dA * cB + cA * dB);
-  const double r2 = k2 * cA * cB + 2.0 * k1 * (dA * cB + cA * dB) + 2.0 * k * dA * dB;
-  f = F * (Tin - cT) + beta * r * V;
-  fx = (-F + beta * V * r1) / V;
-  fF = Tin - cT;
-  fxx = beta * r2 / V;
-  fxF = -1.0 / V;
+  const double cT = x * m.iV;
+  const double d = m.T_in - cT;
+  const double iT = 1.0 / cT;
+  const double g = EaR * iT;
+  const double k = m.k0 * expr(-g);
+  const double cA = fma(d, m.ib, m.cA_in), cB = fma(d, m.ib2, m.cB_in);
+  const double p = cA * cB;
+  const double r = k * p;
+  const double ibw = fma(m.rw1, d, m.rw0);
+  const double k1 = k * (g * iT);
+  const double k2 = k1 * (iT * (g - 2.0));
+  const double r1 = fma(k1, p, -(k * ibw));
+  const double r2 = fma(k2, p, fma(-2.0 * k1, ibw, k * m.rw1));
+  f = fma(m.bV, r, F * d);
+  fx = fma(m.beta, r1, -(F * m.iV));
+  fF = d;
+  fxx = m.beta * r2 * m.iV;
+  fxF = -m.iV;
 }
 
 // One shooting interval (n_rk4 RK4 steps) with first- and second-order
