@@ -31,24 +31,32 @@ __host__ __device__ constexpr int s3(int i, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// Model: drift of Eq. (CSTR), its Jacobian J = df/dn and df/dF.
+// Model: drift of Eq. (CSTR), its Jacobian J = df/dn and df/dF.  With
+// r = k c_A c_B, k = k_0 exp(-g), g = (E_a/R) / c_T, the reaction term is
+// S_p r V (S = (-1, -2, beta)) and its partials in n are (k c_B, k c_A,
+// r g / c_T); one reciprocal, 1 / c_T, serves the whole evaluation.
 __device__ __forceinline__ void drift3(const DevModel& m, double EaR, double T_in,
                                        const double n[3], double F, double f[3], double J[9],
                                        double fF[3]) {
-  const double V = m.V;
-  const double cA = n[0] / V, cB = n[1] / V, cT = n[2] / V;
-  const double k = m.k0 * expr(-EaR / cT);
-  const double rV = k * cA * cB * V;
+  const double iV = m.iV;
+  const double cA = n[0] * iV, cB = n[1] * iV, cT = n[2] * iV;
+  const double iT = 1.0 / cT;
+  const double g = EaR * iT;
+  const double k = m.k0 * expr(-g);
+  const double kcB = k * cB;
+  const double r = kcB * cA;
+  const double rV = r * m.V;
   const double S[3] = {-1.0, -2.0, m.beta};
   const double cin[3] = {m.cA_in, m.cB_in, T_in};
   const double c[3] = {cA, cB, cT};
-  const double drv[3] = {k * cB, k * cA, rV * EaR / (cT * cT) / V};
+  const double drv[3] = {kcB, k * cA, r * (g * iT)};
+  const double nFiV = -(F * iV);
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    f[p] = cin[p] * F - c[p] * F + S[p] * rV;
     fF[p] = cin[p] - c[p];
+    f[p] = fma(fF[p], F, S[p] * rV);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) J[p * 3 + q] = (p == q ? -F / V : 0.0) + S[p] * drv[q];
+    for (int q = 0; q < 3; ++q) J[p * 3 + q] = (p == q) ? fma(S[p], drv[q], nFiV) : S[p] * drv[q];
   }
 }
 
