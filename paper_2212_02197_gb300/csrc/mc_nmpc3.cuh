@@ -465,7 +465,7 @@ __device__ __noinline__ QpResult qp3_active_set(const Ws& w, int N, int max_it) 
 __device__ __noinline__ double evaluate3(const DevModel& m, const DevCtrl& c, double EaR, int N,
                                          const Ws& w, int u_arr, int x_arr, int a_arr,
                                          int b_arr, int g_arr, int q_arr) {
-  const double xs = c.x_scale;
+  const double xs = c.x_scale, ixs = 1.0 / c.x_scale, sz = c.x_scale * m.iV;
   double f = 0.0;
   for (int k = 0; k < N; ++k) {
     double n0[3], Fn[3], A[9], B[3];
@@ -474,17 +474,17 @@ __device__ __noinline__ double evaluate3(const DevModel& m, const DevCtrl& c, do
     rk4_interval3(m, EaR, c.n_rk4, m.Ts, n0, w(u_arr, k), c.Fconv, Fn, A, B);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      w(b_arr + i, k) = B[i] / xs;
-      w(g_arr + i, k) = Fn[i] / xs - w(x_arr + i, k + 1);
+      w(b_arr + i, k) = B[i] * ixs;
+      w(g_arr + i, k) = Fn[i] * ixs - w(x_arr + i, k + 1);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) w(a_arr + i, k) = A[i];
   }
   w(q_arr, 0) = 0.0;
   for (int k = 1; k <= N; ++k) {
-    const double dz = w(x_arr + 2, k) * xs / m.V - w(ZB3, k);
+    const double dz = w(x_arr + 2, k) * sz - w(ZB3, k);
     f += c.Qz * dz * dz * m.Ts;
-    w(q_arr, k) = 2.0 * c.Qz * dz * m.Ts * xs / m.V;
+    w(q_arr, k) = 2.0 * c.Qz * dz * m.Ts * sz;
   }
   return f;
 }
@@ -507,9 +507,10 @@ __device__ __forceinline__ void bfgs_blockn(int n, double* W, const double* s, c
     sr += s[i] * rr[i];
   }
   if (!(fmin(sWs, sr) > eps_m)) return;
+  const double isWs = 1.0 / sWs, isr = 1.0 / sr;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
-      W[i * 4 + j] = W[i * 4 + j] - Ws[i] * Ws[j] / sWs + rr[i] * rr[j] / sr;
+      W[i * 4 + j] = W[i * 4 + j] - Ws[i] * Ws[j] * isWs + rr[i] * rr[j] * isr;
 }
 
 __device__ __forceinline__ bool chol_pd(int n, const double* W) {
@@ -521,10 +522,11 @@ __device__ __forceinline__ bool chol_pd(int n, const double* W) {
     if (!(d > 0.0)) return false;
     d = sqrt(d);
     a[j * 4 + j] = d;
+    const double id = 1.0 / d;
     for (int i = j + 1; i < n; ++i) {
       double s = a[i * 4 + j];
       for (int k = 0; k < j; ++k) s -= a[i * 4 + k] * a[j * 4 + k];
-      a[i * 4 + j] = s / d;
+      a[i * 4 + j] = s * id;
     }
   }
   return true;
@@ -704,12 +706,13 @@ __device__ __noinline__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, 
       w(GLU3, k) = lagr_gu(w, k);
       for (int i = 0; i < 3; ++i) w(GLX3 + i, k + 1) = lagr_gx(w, k + 1, N, i);
     }
+    const double ialpha = 1.0 / alpha;  // alpha is a power of two: exact
     for (int k = 0; k < N; ++k) {
       const double un = w(UT3, k);
-      w(DU3, k) = (un - w(U3, k)) / alpha;
+      w(DU3, k) = (un - w(U3, k)) * ialpha;
       w(U3, k) = un;
       for (int i = 0; i < 3; ++i) {
-        w(DX3 + i, k + 1) = (w(XT3 + i, k + 1) - w(X3 + i, k + 1)) / alpha;
+        w(DX3 + i, k + 1) = (w(XT3 + i, k + 1) - w(X3 + i, k + 1)) * ialpha;
         w(X3 + i, k + 1) = w(XT3 + i, k + 1);
         w(EB3 + i, k) = w(TB3 + i, k);
         w(EG3 + i, k) = w(TG3 + i, k);

@@ -350,9 +350,10 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
   }
   // accept the trial point and its evaluation; the step actually taken
   // (after the bound clip) is what BFGS sees
+  const double ialpha = 1.0 / alpha;  // alpha is a power of two: exact
   for (int k = 0; k < N; ++k) {
     const double un = w(UT, k);
-    w(DU, k) = (un - w(U, k)) / alpha;
+    w(DU, k) = (un - w(U, k)) * ialpha;
     w(U, k) = un;
     w(X, k + 1) = w(XT, k + 1);
     w(EA, k) = w(TA, k);
