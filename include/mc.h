@@ -119,7 +119,7 @@ typedef struct {
   int32_t nx_model;       /* NMPC model: 0 or 1 = the one-state model of Sec. VI
                              (the paper's); 3 = the three-state model of
                              Eq. (CSTR) with a 3x3 CD-EKF (FP64, active-set
-                             QP, static schedule)                             */
+                             QP, either schedule)                             */
   /* extended NMPC objective (the paper's has both 0):
    *   + sum_{k=1..N} Ru (v_{k-1} - vbar_k)^2 T_s + Qn (z_N - zbar_N)^2,
    * v the OCP input (flow / u_scale), vbar_k the steady-state input of the

@@ -83,6 +83,19 @@ __global__ void __launch_bounds__(32) k_nmpc3(DevModel m, DevCtrl c, int64_t j0,
   }
 }
 
+// The three-state NMPC closed loop on the persistent schedule (one warp per
+// block, every lane in the warp votes of nmpc3_persistent).
+__global__ void __launch_bounds__(32) k_nmpc3_persist(DevModel m, DevCtrl c, int64_t j0,
+                                                      int64_t n, const uint32_t* order,
+                                                      unsigned long long* next,
+                                                      double* __restrict__ phi,
+                                                      int32_t* __restrict__ cnt, double* ws,
+                                                      int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Ws w{ws + t, ld, c.N + 1};
+  nmpc3_persistent(m, c, w, j0, n, order, next, phi, cnt);
+}
+
 template <class R>
 __global__ void __launch_bounds__(32) k_nmpc_persist(DevModel m, DevCtrl c, int64_t j0,
                                                      int64_t n, const uint32_t* order,
@@ -561,11 +574,8 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
       return bad("the objective weights Ru and Qn must be finite and >= 0");
     if (cc->nx_model == 3 && (cc->Ru != 0.0 || cc->Qn != 0.0))
       return bad("the three-state NMPC has the paper's objective only (Ru = Qn = 0)");
-    if (cc->nx_model == 3 &&
-        (cc->precision != MC_FP64 || cc->qp_solver != MC_QP_ACTIVE_SET ||
-         cc->schedule != MC_SCHED_STATIC))
-      return bad("the three-state NMPC runs in FP64 with the active-set QP and the static "
-                 "schedule");
+    if (cc->nx_model == 3 && (cc->precision != MC_FP64 || cc->qp_solver != MC_QP_ACTIVE_SET))
+      return bad("the three-state NMPC runs in FP64 with the active-set QP");
   }
   memset(m, 0, sizeof(*m));
   m->V = mm->V; m->k0 = mm->k0; m->EaR = mm->EaR; m->beta = mm->beta;
@@ -790,7 +800,10 @@ static mc_status enqueue_run(mc_handle* h, const DevModel& m, int64_t j0, int64_
       const uint32_t* order = (j0 == 0 && j1 == h->n_sims) ? h->order : nullptr;
       MC_CUDA(h, cudaMemsetAsync(h->next, 0, sizeof(unsigned long long), st));
       const unsigned blocks = (unsigned)(threads / kNmpcThreads);
-      if (h->c.precision == MC_FP64)
+      if (h->c.nx_model == 3)
+        k_nmpc3_persist<<<blocks, kNmpcThreads, 0, st>>>(m, h->c, j0, n, order, h->next, h->phi,
+                                                         h->cnt, h->ws, h->ws_ld);
+      else if (h->c.precision == MC_FP64)
         k_nmpc_persist<double><<<blocks, kNmpcThreads, 0, st>>>(
             m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz);
       else

@@ -460,26 +460,33 @@ __device__ __noinline__ QpResult qp3_active_set(const Ws& w, int N, int max_it) 
 // ---------------------------------------------------------------------------
 // SQP for the three-state OCP.
 
-// Shooting of all intervals at (u_arr, x_arr) with sensitivities into
-// (a_arr, b_arr, g_arr) and the temperature part of q into q_arr; returns f.
-__device__ __noinline__ double evaluate3(const DevModel& m, const DevCtrl& c, double EaR, int N,
-                                         const Ws& w, int u_arr, int x_arr, int a_arr,
-                                         int b_arr, int g_arr, int q_arr) {
-  const double xs = c.x_scale, ixs = 1.0 / c.x_scale, sz = c.x_scale * m.iV;
-  double f = 0.0;
-  for (int k = 0; k < N; ++k) {
-    double n0[3], Fn[3], A[9], B[3];
+// Shooting of interval k at (u_arr, x_arr) with sensitivities into (a_arr,
+// b_arr, g_arr).  Not inlined: evaluate3 and the persistent schedule's pool
+// (any lane shooting any lane's interval) run this one compiled body, so both
+// give the same bits.
+__device__ __noinline__ void shoot3_interval(const DevModel& m, const DevCtrl& c, double EaR,
+                                             const Ws& w, int k, int u_arr, int x_arr,
+                                             int a_arr, int b_arr, int g_arr) {
+  const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
+  double n0[3], Fn[3], A[9], B[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) n0[i] = ((k == 0) ? w(X3 + i, 0) : w(x_arr + i, k)) * xs;
-    rk4_interval3(m, EaR, c.n_rk4, m.Ts, n0, w(u_arr, k), c.Fconv, Fn, A, B);
+  for (int i = 0; i < 3; ++i) n0[i] = ((k == 0) ? w(X3 + i, 0) : w(x_arr + i, k)) * xs;
+  rk4_interval3(m, EaR, c.n_rk4, m.Ts, n0, w(u_arr, k), c.Fconv, Fn, A, B);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      w(b_arr + i, k) = B[i] * ixs;
-      w(g_arr + i, k) = Fn[i] * ixs - w(x_arr + i, k + 1);
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) w(a_arr + i, k) = A[i];
+  for (int i = 0; i < 3; ++i) {
+    w(b_arr + i, k) = B[i] * ixs;
+    w(g_arr + i, k) = Fn[i] * ixs - w(x_arr + i, k + 1);
   }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) w(a_arr + i, k) = A[i];
+}
+
+// The objective at the states x_arr and the temperature part of q into
+// q_arr (the intervals already shot); returns f.
+__device__ __noinline__ double evaluate3_obj(const DevModel& m, const DevCtrl& c, int N,
+                                             const Ws& w, int x_arr, int q_arr) {
+  const double sz = c.x_scale * m.iV;
+  double f = 0.0;
   w(q_arr, 0) = 0.0;
   for (int k = 1; k <= N; ++k) {
     const double dz = w(x_arr + 2, k) * sz - w(ZB3, k);
@@ -487,6 +494,15 @@ __device__ __noinline__ double evaluate3(const DevModel& m, const DevCtrl& c, do
     w(q_arr, k) = 2.0 * c.Qz * dz * m.Ts * sz;
   }
   return f;
+}
+
+// Shooting of all intervals at (u_arr, x_arr) with sensitivities into
+// (a_arr, b_arr, g_arr) and the temperature part of q into q_arr; returns f.
+__device__ __forceinline__ double evaluate3(const DevModel& m, const DevCtrl& c, double EaR,
+                                            int N, const Ws& w, int u_arr, int x_arr, int a_arr,
+                                            int b_arr, int g_arr, int q_arr) {
+  for (int k = 0; k < N; ++k) shoot3_interval(m, c, EaR, w, k, u_arr, x_arr, a_arr, b_arr, g_arr);
+  return evaluate3_obj(m, c, N, w, x_arr, q_arr);
 }
 
 // damped BFGS of an n x n symmetric block held in registers (n <= 4)
@@ -613,129 +629,198 @@ __device__ __noinline__ bool bfgs3_pass(const Ws& w, int N, double alpha) {
   return pd;
 }
 
-// The SQP of Sec. IV for one three-state OCP from the warm start in (U3, X3,
-// LAM3, PIL3, PIU3) with x_0 in X3(., 0) and the set-points in ZB3.
-__device__ __noinline__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, double EaR, const Ws& w,
-                              int N, int max_it) {
-  const double c1 = 1e-4, s_max = 100.0;
-  SqpInfo info{};
+// The SQP of Sec. IV for one three-state OCP, as resumable phases (as for the
+// one-state OCP in mc_sqp.cuh):
+//   sqp3_begin         W = I; the first evaluation at the warm start follows
+//   sqp3_check         block BFGS, the scaled KKT test, the QP, the merit
+//                      slope, and the first trial point
+//   (shooting of the trial point)
+//   sqp3_trial_result  Armijo test; accept and step, or halve the step
+// sqp3_solve chains them for one OCP.
+struct Sqp3State {
+  int N, max_it, l, hv;
+  double f, ft, alpha, T0, DT0;
+  SqpInfo info;
+};
+
+__device__ __forceinline__ void sqp3_begin(const Ws& w, int N, int max_it, Sqp3State& st) {
   identity_blocks(w, N);
-  double f = evaluate3(m, c, EaR, N, w, U3, X3, EA3, EB3, EG3, EQ3);
-  double alpha = 0.0;
-  for (int l = 0;; ++l) {
-    if (l > 0 && !bfgs3_pass(w, N, alpha)) {
-      identity_blocks(w, N);
-      info.n_hess_reset++;
-    }
-    // scaled convergence test
-    double mult1 = 0.0, kg = 0.0, ke = 0.0;
-    for (int k = 0; k < N; ++k) {
-      mult1 += fabs(w(PIL3, k)) + fabs(w(PIU3, k));
-      for (int i = 0; i < 3; ++i) mult1 += fabs(w(LAM3 + i, k));
-      kg = fmax(kg, fabs(lagr_gu(w, k)));
-      for (int i = 0; i < 3; ++i) {
-        kg = fmax(kg, fabs(lagr_gx(w, k + 1, N, i)));
-        ke = fmax(ke, fabs(w(EG3 + i, k)));
-      }
-    }
-    const double s_d = fmax(s_max, mult1 / (5.0 * N)) / s_max;
-    kg /= s_d;
-    info.kkt_grad = kg;
-    info.kkt_eq = ke;
-    info.f = f;
-    if (kg <= c.sqp_tol && ke <= c.sqp_tol) {
-      info.status = 0;
-      break;
-    }
-    if (l >= max_it) {
-      info.status = 1;
-      break;
-    }
-    // QP at xi^[l]
-    for (int k = 0; k < N; ++k) {
-      const double u = w(U3, k);
-      w(LB3, k) = c.vmin - u;
-      w(UB3, k) = c.vmax - u;
-    }
-    const QpResult qr = qp3_active_set(w, N, 10 * N + 20);
-    info.qp_iters += qr.iters;
-    if (qr.status != 0) info.qp_fail++;
-    info.iters++;
-    double pen = 0.0, dfd = 0.0;
-    for (int k = 0; k < N; ++k)
-      for (int i = 0; i < 3; ++i) {
-        const double am = fabs(w(MU3 + i, k));
-        const double sg = (l == 0) ? am : fmax(am, 0.5 * (w(SIG3 + i, k) + am));
-        w(SIG3 + i, k) = sg;
-        pen += sg * fabs(w(EG3 + i, k));
-      }
-    for (int k = 1; k <= N; ++k) dfd += w(EQ3, k) * w(DX3 + 2, k);
-    const double T0 = f + pen, DT0 = dfd - pen;
-    // backtracking
-    alpha = 1.0;
-    bool accepted = false;
-    double ft = 0.0;
-    for (int hv = 0; hv <= c.ls_max; ++hv) {
-      for (int k = 0; k < N; ++k) {
-        w(UT3, k) = fmin(fmax(w(U3, k) + alpha * w(DU3, k), c.vmin), c.vmax);
-        for (int i = 0; i < 3; ++i) w(XT3 + i, k + 1) = w(X3 + i, k + 1) + alpha * w(DX3 + i, k + 1);
-      }
-      ft = evaluate3(m, c, EaR, N, w, UT3, XT3, TA3, TB3, TG3, TQ3);
-      info.ls_trials++;
-      double pt = 0.0;
-      for (int k = 0; k < N; ++k)
-        for (int i = 0; i < 3; ++i) pt += w(SIG3 + i, k) * fabs(w(TG3 + i, k));
-      if (ft + pt <= T0 + c1 * alpha * DT0) {
-        accepted = true;
-        break;
-      }
-      alpha *= 0.5;
-    }
-    if (!accepted) {
-      info.status = 2;
-      break;
-    }
-    // multipliers, old-point gradient at the new multipliers, accept the point
-    for (int k = 0; k < N; ++k) {
-      for (int i = 0; i < 3; ++i)
-        w(LAM3 + i, k) = w(LAM3 + i, k) + alpha * (w(MU3 + i, k) - w(LAM3 + i, k));
-      w(PIL3, k) = w(PIL3, k) + alpha * (w(NUL3, k) - w(PIL3, k));
-      w(PIU3, k) = w(PIU3, k) + alpha * (w(NUU3, k) - w(PIU3, k));
-    }
-    for (int k = 0; k < N; ++k) {
-      w(GLU3, k) = lagr_gu(w, k);
-      for (int i = 0; i < 3; ++i) w(GLX3 + i, k + 1) = lagr_gx(w, k + 1, N, i);
-    }
-    const double ialpha = 1.0 / alpha;  // alpha is a power of two: exact
-    for (int k = 0; k < N; ++k) {
-      const double un = w(UT3, k);
-      w(DU3, k) = (un - w(U3, k)) * ialpha;
-      w(U3, k) = un;
-      for (int i = 0; i < 3; ++i) {
-        w(DX3 + i, k + 1) = (w(XT3 + i, k + 1) - w(X3 + i, k + 1)) * ialpha;
-        w(X3 + i, k + 1) = w(XT3 + i, k + 1);
-        w(EB3 + i, k) = w(TB3 + i, k);
-        w(EG3 + i, k) = w(TG3 + i, k);
-      }
-      for (int i = 0; i < 9; ++i) w(EA3 + i, k) = w(TA3 + i, k);
-      w(EQ3, k + 1) = w(TQ3, k + 1);
-    }
-    f = ft;
+  st.N = N;
+  st.max_it = max_it;
+  st.l = 0;
+  st.hv = 0;
+  st.f = st.ft = st.alpha = st.T0 = st.DT0 = 0.0;
+  st.info = SqpInfo{};
+}
+
+// Trial point xi + alpha dxi (u clipped into its bounds against rounding).
+__device__ __forceinline__ void sqp3_trial_point(const DevCtrl& c, const Ws& w,
+                                                 const Sqp3State& st) {
+  for (int k = 0; k < st.N; ++k) {
+    w(UT3, k) = fmin(fmax(w(U3, k) + st.alpha * w(DU3, k), c.vmin), c.vmax);
+    for (int i = 0; i < 3; ++i)
+      w(XT3 + i, k + 1) = w(X3 + i, k + 1) + st.alpha * w(DX3 + i, k + 1);
   }
-  return info;
+}
+
+// Top of an SQP iteration at xi^[l] (evaluated, f in st.f).  Returns true when
+// the OCP is finished (st.info.status set); else prepares the first trial.
+__device__ __noinline__ bool sqp3_check(const DevCtrl& c, const Ws& w, Sqp3State& st) {
+  const int N = st.N;
+  const double s_max = 100.0;
+  if (st.l > 0 && !bfgs3_pass(w, N, st.alpha)) {
+    identity_blocks(w, N);
+    st.info.n_hess_reset++;
+  }
+  // scaled convergence test
+  double mult1 = 0.0, kg = 0.0, ke = 0.0;
+  for (int k = 0; k < N; ++k) {
+    mult1 += fabs(w(PIL3, k)) + fabs(w(PIU3, k));
+    for (int i = 0; i < 3; ++i) mult1 += fabs(w(LAM3 + i, k));
+    kg = fmax(kg, fabs(lagr_gu(w, k)));
+    for (int i = 0; i < 3; ++i) {
+      kg = fmax(kg, fabs(lagr_gx(w, k + 1, N, i)));
+      ke = fmax(ke, fabs(w(EG3 + i, k)));
+    }
+  }
+  const double s_d = fmax(s_max, mult1 / (5.0 * N)) / s_max;
+  kg /= s_d;
+  st.info.kkt_grad = kg;
+  st.info.kkt_eq = ke;
+  st.info.f = st.f;
+  if (kg <= c.sqp_tol && ke <= c.sqp_tol) {
+    st.info.status = 0;
+    return true;
+  }
+  if (st.l >= st.max_it) {
+    st.info.status = 1;
+    return true;
+  }
+  // QP at xi^[l]
+  for (int k = 0; k < N; ++k) {
+    const double u = w(U3, k);
+    w(LB3, k) = c.vmin - u;
+    w(UB3, k) = c.vmax - u;
+  }
+  const QpResult qr = qp3_active_set(w, N, 10 * N + 20);
+  st.info.qp_iters += qr.iters;
+  if (qr.status != 0) st.info.qp_fail++;
+  st.info.iters++;
+  double pen = 0.0, dfd = 0.0;
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i < 3; ++i) {
+      const double am = fabs(w(MU3 + i, k));
+      const double sg = (st.l == 0) ? am : fmax(am, 0.5 * (w(SIG3 + i, k) + am));
+      w(SIG3 + i, k) = sg;
+      pen += sg * fabs(w(EG3 + i, k));
+    }
+  for (int k = 1; k <= N; ++k) dfd += w(EQ3, k) * w(DX3 + 2, k);
+  st.T0 = st.f + pen;
+  st.DT0 = dfd - pen;
+  st.alpha = 1.0;
+  st.hv = 0;
+  sqp3_trial_point(c, w, st);
+  return false;
+}
+
+// Armijo test of the evaluated trial point (st.ft; its shooting in TA3, TB3,
+// TG3, TQ3).  Returns 0 when the step was accepted (continue with
+// sqp3_check), 1 when the line search ran out of halvings (status 2; the OCP
+// is finished at the current iterate), 2 when the step was halved (evaluate
+// the new trial point).
+__device__ __noinline__ int sqp3_trial_result(const DevCtrl& c, const Ws& w, Sqp3State& st) {
+  const int N = st.N;
+  const double c1 = 1e-4;
+  st.info.ls_trials++;
+  double pt = 0.0;
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i < 3; ++i) pt += w(SIG3 + i, k) * fabs(w(TG3 + i, k));
+  if (!(st.ft + pt <= st.T0 + c1 * st.alpha * st.DT0)) {
+    st.alpha *= 0.5;
+    st.hv++;
+    if (st.hv > c.ls_max) {
+      st.info.status = 2;
+      return 1;
+    }
+    sqp3_trial_point(c, w, st);
+    return 2;
+  }
+  const double alpha = st.alpha;
+  // multipliers, old-point gradient at the new multipliers, accept the point
+  for (int k = 0; k < N; ++k) {
+    for (int i = 0; i < 3; ++i)
+      w(LAM3 + i, k) = w(LAM3 + i, k) + alpha * (w(MU3 + i, k) - w(LAM3 + i, k));
+    w(PIL3, k) = w(PIL3, k) + alpha * (w(NUL3, k) - w(PIL3, k));
+    w(PIU3, k) = w(PIU3, k) + alpha * (w(NUU3, k) - w(PIU3, k));
+  }
+  for (int k = 0; k < N; ++k) {
+    w(GLU3, k) = lagr_gu(w, k);
+    for (int i = 0; i < 3; ++i) w(GLX3 + i, k + 1) = lagr_gx(w, k + 1, N, i);
+  }
+  const double ialpha = 1.0 / alpha;  // alpha is a power of two: exact
+  for (int k = 0; k < N; ++k) {
+    const double un = w(UT3, k);
+    w(DU3, k) = (un - w(U3, k)) * ialpha;
+    w(U3, k) = un;
+    for (int i = 0; i < 3; ++i) {
+      w(DX3 + i, k + 1) = (w(XT3 + i, k + 1) - w(X3 + i, k + 1)) * ialpha;
+      w(X3 + i, k + 1) = w(XT3 + i, k + 1);
+      w(EB3 + i, k) = w(TB3 + i, k);
+      w(EG3 + i, k) = w(TG3 + i, k);
+    }
+    for (int i = 0; i < 9; ++i) w(EA3 + i, k) = w(TA3 + i, k);
+    w(EQ3, k + 1) = w(TQ3, k + 1);
+  }
+  st.f = st.ft;
+  st.l++;
+  return 0;
+}
+
+// One three-state OCP from the warm start in (U3, X3, LAM3, PIL3, PIU3) with
+// x_0 in X3(., 0) and the set-points in ZB3.
+__device__ __noinline__ SqpInfo sqp3_solve(const DevModel& m, const DevCtrl& c, double EaR,
+                                           const Ws& w, int N, int max_it) {
+  Sqp3State st;
+  sqp3_begin(w, N, max_it, st);
+  st.f = evaluate3(m, c, EaR, N, w, U3, X3, EA3, EB3, EG3, EQ3);
+  while (!sqp3_check(c, w, st)) {
+    int r;
+    do {
+      st.ft = evaluate3(m, c, EaR, N, w, UT3, XT3, TA3, TB3, TG3, TQ3);
+      r = sqp3_trial_result(c, w, st);
+    } while (r == 2);
+    if (r == 1) break;
+  }
+  return st.info;
 }
 
 // ---------------------------------------------------------------------------
 // Closed loop with the three-state NMPC (plant, measurement, Phi as in
-// traj_nmpc; FP64 only).
-__device__ TrajOut traj_nmpc3(const DevModel& m, const DevCtrl& c, uint32_t j, const Ws& w) {
-  TrajOut out{};
-  const TrajParams tp = traj_params(m, c, j);
-  const int N = tp.N, K = m.n_steps;
-  double n[3] = {m.cA_in * m.V, m.cB_in * m.V, m.T_in * m.V};
-  double xh[3] = {n[0], n[1], n[2]};
-  double P[6] = {c.P0, 0.0, 0.0, c.P0, 0.0, c.P0};
-  double v0 = Fss(m, tp.EaR_c, zbar(m, m.t0)) / c.Fconv;
+// traj_nmpc; FP64 only), split into the steps both schedules share.
+
+struct Nmpc3Traj {
+  uint32_t j;
+  int i;                   // current sample
+  TrajParams tp;
+  double n[3], xh[3], P[6], F_prev, phi;
+  TrajOut out;
+};
+
+__device__ __forceinline__ void nmpc3_begin(const DevModel& m, const DevCtrl& c, uint32_t j,
+                                            const Ws& w, Nmpc3Traj& T) {
+  T.j = j;
+  T.i = 0;
+  T.tp = traj_params(m, c, j);
+  const int N = T.tp.N;
+  T.n[0] = m.cA_in * m.V;
+  T.n[1] = m.cB_in * m.V;
+  T.n[2] = m.T_in * m.V;
+  for (int q = 0; q < 3; ++q) T.xh[q] = T.n[q];
+  T.P[0] = c.P0; T.P[1] = 0.0; T.P[2] = 0.0; T.P[3] = c.P0; T.P[4] = 0.0; T.P[5] = c.P0;
+  T.F_prev = 0.0;
+  T.phi = 0.0;
+  T.out = TrajOut{};
+  double v0 = Fss(m, T.tp.EaR_c, zbar(m, m.t0)) / c.Fconv;
   v0 = fmin(fmax(v0, c.vmin), c.vmax);
   for (int k = 0; k < N; ++k) {
     w(U3, k) = v0;
@@ -744,50 +829,196 @@ __device__ TrajOut traj_nmpc3(const DevModel& m, const DevCtrl& c, uint32_t j, c
     for (int i = 0; i < 3; ++i) w(LAM3 + i, k) = 0.0;
   }
   for (int k = 0; k <= N; ++k)
-    for (int i = 0; i < 3; ++i) w(X3 + i, k) = xh[i] / c.x_scale;
-  double phi = 0.0, F_prev = 0.0;
-  for (int i = 0; i <= K; ++i) {
-    const double t_i = m.t0 + (double)i * m.Ts;
-    const double cT = n[2] / m.V;
-    bool bad = !isfinite(cT);
-    for (int q = 0; q < 3; ++q) bad = bad || !isfinite(xh[q]);
-    for (int q = 0; q < 6; ++q) bad = bad || !isfinite(P[q]);
-    if (bad) {
-      out.cnt[6] = 1;
-      out.phi = nan("");
-      return out;
+    for (int i = 0; i < 3; ++i) w(X3 + i, k) = T.xh[i] / c.x_scale;
+}
+
+// Sample i: Phi term, and unless the trajectory ends there the measurement,
+// the CD-EKF and the start of the OCP (its first evaluation is the caller's).
+// Returns false when the trajectory is finished (T.out is final).
+__device__ __noinline__ bool nmpc3_sample(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                          Nmpc3Traj& T, Sqp3State& st) {
+  const int N = T.tp.N, K = m.n_steps, i = T.i;
+  const double t_i = m.t0 + (double)i * m.Ts;
+  const double cT = T.n[2] / m.V;
+  bool bad = !isfinite(cT);
+  for (int q = 0; q < 3; ++q) bad = bad || !isfinite(T.xh[q]);
+  for (int q = 0; q < 6; ++q) bad = bad || !isfinite(T.P[q]);
+  if (bad) {
+    T.out.cnt[6] = 1;
+    T.out.phi = nan("");
+    return false;
+  }
+  const double ez = cT - zbar(m, t_i);
+  T.phi += ez * ez;
+  if (i == K) {
+    T.out.phi = T.phi / (double)(K + 1);
+    return false;
+  }
+  const double y = cT + m.meas_sd * meas_noise<double>(m, T.j, (uint32_t)i);
+  if (i > 0) ekf3_predict(m, T.tp.EaR_c, c.n_rk4, T.F_prev, T.xh, T.P);
+  ekf3_filter(m, y, T.xh, T.P);
+  for (int k = 1; k <= N; ++k) w(ZB3, k) = zbar(m, m.t0 + (double)(i + k) * m.Ts);
+  for (int q = 0; q < 3; ++q) w(X3 + q, 0) = T.xh[q] / c.x_scale;
+  sqp3_begin(w, N, T.tp.max_it, st);
+  return true;
+}
+
+// After the OCP of sample i: count it, apply u_0, shift the warm start,
+// simulate the plant to t_{i+1}.
+__device__ __noinline__ void nmpc3_apply(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                         Nmpc3Traj& T, const SqpInfo& si) {
+  const int N = T.tp.N;
+  T.out.cnt[0] += (si.status == 1);
+  T.out.cnt[1] += si.iters;
+  T.out.cnt[2] += si.ls_trials;
+  T.out.cnt[3] += si.n_hess_reset;
+  T.out.cnt[4] += (si.status == 2);
+  T.out.cnt[5] += si.qp_iters;
+  T.out.cnt[7] += si.qp_fail;
+  const double F = w(U3, 0) * c.Fconv;
+  for (int k = 0; k < N - 1; ++k) {
+    w(U3, k) = w(U3, k + 1);
+    w(PIL3, k) = w(PIL3, k + 1);
+    w(PIU3, k) = w(PIU3, k + 1);
+    for (int q = 0; q < 3; ++q) {
+      w(X3 + q, k + 1) = w(X3 + q, k + 2);
+      w(LAM3 + q, k) = w(LAM3 + q, k + 1);
     }
-    const double ez = cT - zbar(m, t_i);
-    phi += ez * ez;
-    if (i == K) break;
-    const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
-    if (i > 0) ekf3_predict(m, tp.EaR_c, c.n_rk4, F_prev, xh, P);
-    ekf3_filter(m, y, xh, P);
-    for (int k = 1; k <= N; ++k) w(ZB3, k) = zbar(m, m.t0 + (double)(i + k) * m.Ts);
-    for (int q = 0; q < 3; ++q) w(X3 + q, 0) = xh[q] / c.x_scale;
-    const SqpInfo si = sqp3_solve(m, c, tp.EaR_c, w, N, tp.max_it);
-    out.cnt[0] += (si.status == 1);
-    out.cnt[1] += si.iters;
-    out.cnt[2] += si.ls_trials;
-    out.cnt[3] += si.n_hess_reset;
-    out.cnt[4] += (si.status == 2);
-    out.cnt[5] += si.qp_iters;
-    out.cnt[7] += si.qp_fail;
-    const double F = w(U3, 0) * c.Fconv;
-    for (int k = 0; k < N - 1; ++k) {
-      w(U3, k) = w(U3, k + 1);
-      w(PIL3, k) = w(PIL3, k + 1);
-      w(PIU3, k) = w(PIU3, k + 1);
-      for (int q = 0; q < 3; ++q) {
-        w(X3 + q, k + 1) = w(X3 + q, k + 2);
-        w(LAM3 + q, k) = w(LAM3 + q, k + 1);
+  }
+  plant_interval<double>(m, T.tp, T.j, T.i, F, T.n);
+  T.F_prev = F;
+  T.i++;
+}
+
+// Static schedule: one trajectory per thread, the OCPs run to completion.
+__device__ TrajOut traj_nmpc3(const DevModel& m, const DevCtrl& c, uint32_t j, const Ws& w) {
+  Nmpc3Traj T;
+  Sqp3State st;
+  nmpc3_begin(m, c, j, w, T);
+  while (nmpc3_sample(m, c, w, T, st)) {
+    st.f = evaluate3(m, c, T.tp.EaR_c, st.N, w, U3, X3, EA3, EB3, EG3, EQ3);
+    while (!sqp3_check(c, w, st)) {
+      int r;
+      do {
+        st.ft = evaluate3(m, c, T.tp.EaR_c, st.N, w, UT3, XT3, TA3, TB3, TG3, TQ3);
+        r = sqp3_trial_result(c, w, st);
+      } while (r == 2);
+      if (r == 1) break;
+    }
+    nmpc3_apply(m, c, w, T, st.info);
+  }
+  return T.out;
+}
+
+// Persistent schedule, as nmpc_persistent for the one-state NMPC: every lane
+// runs its cheap phases until it needs shooting (a trial point, or the first
+// evaluation of a new OCP), then the warp shoots all pending intervals as one
+// pool, interval-major, lane t taking jobs t, t + 32, ...; each job is one
+// call of shoot3_interval, so the results are those of the static schedule
+// bit for bit.  Every lane of the warp must call this; the block is one warp.
+enum Lane3Phase : int { k3New = 0, k3Sample = 1, k3Check = 2, k3Trial = 3, k3Start = 4, k3Done = 5 };
+
+struct Pool3Tab {
+  unsigned mask[MC_MAX_HORIZON];  // lanes with a job at position i
+  int pref[MC_MAX_HORIZON];       // jobs before position i
+  double EaR[32];
+  int trial[32];
+};
+
+__device__ __forceinline__ void pool3_shoot(const DevModel& m, const DevCtrl& c, const Ws& w,
+                                            int n_jobs, bool trial, double EaR, Pool3Tab& tab) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int max_jobs = (int)__reduce_max_sync(full, (unsigned)n_jobs);
+  __syncwarp();  // the previous round's readers of tab are done
+  tab.EaR[lane] = EaR;
+  tab.trial[lane] = trial ? 1 : 0;
+  int total = 0;
+  for (int i = 0; i < max_jobs; ++i) {
+    const unsigned mi = __ballot_sync(full, n_jobs > i);
+    if (lane == 0) {
+      tab.mask[i] = mi;
+      tab.pref[i] = total;
+    }
+    total += __popc(mi);
+  }
+  __syncwarp();  // tab and the owners' points are visible to every lane
+  for (int q = lane; q < total; q += 32) {
+    int lo = 0, hi = max_jobs;  // pref[lo] <= q < pref[hi], pref[max_jobs] = total
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tab.pref[mid] <= q) lo = mid;
+      else hi = mid;
+    }
+    unsigned mo = tab.mask[lo];
+    for (int r = q - tab.pref[lo]; r > 0; --r) mo &= mo - 1u;
+    const int o = __ffs(mo) - 1;
+    const bool tr = tab.trial[o] != 0;
+    const Ws wo{w.p + (o - lane), w.ld, w.N1};
+    shoot3_interval(m, c, tab.EaR[o], wo, lo, tr ? UT3 : U3, tr ? XT3 : X3, tr ? TA3 : EA3,
+                    tr ? TB3 : EB3, tr ? TG3 : EG3);
+  }
+  __syncwarp();  // the shot intervals are visible to their owners
+}
+
+__device__ void nmpc3_persistent(const DevModel& m, const DevCtrl& c, const Ws& w, int64_t j0,
+                                 int64_t n, const uint32_t* __restrict__ order,
+                                 unsigned long long* next, double* __restrict__ phi_out,
+                                 int32_t* __restrict__ cnt_out) {
+  __shared__ Pool3Tab tab;  // one per block: the kernel runs one warp per block
+  Nmpc3Traj T;
+  Sqp3State st;
+  int phase = k3New;
+  for (;;) {
+    while (phase != k3Trial && phase != k3Start && phase != k3Done) {
+      if (phase == k3New) {
+        const unsigned long long q = atomicAdd(next, 1ull);
+        if (q >= (unsigned long long)n) {
+          phase = k3Done;
+          break;
+        }
+        const uint32_t j = order ? order[q] : (uint32_t)(j0 + (int64_t)q);
+        nmpc3_begin(m, c, j, w, T);
+        phase = k3Sample;
+      }
+      if (phase == k3Sample) {
+        if (nmpc3_sample(m, c, w, T, st)) {
+          phase = k3Start;
+        } else {
+          phi_out[T.j] = T.out.phi;
+#pragma unroll
+          for (int q = 0; q < kNCounters; ++q)
+            cnt_out[(int64_t)T.j * kNCounters + q] = T.out.cnt[q];
+          phase = k3New;
+        }
+        continue;
+      }
+      if (phase == k3Check) {
+        if (sqp3_check(c, w, st)) {
+          nmpc3_apply(m, c, w, T, st.info);
+          phase = k3Sample;
+        } else {
+          phase = k3Trial;
+        }
       }
     }
-    plant_interval<double>(m, tp, j, i, F, n);
-    F_prev = F;
+    if (!__ballot_sync(0xffffffffu, phase != k3Done)) break;
+    const int n_jobs = (phase == k3Trial || phase == k3Start) ? st.N : 0;
+    pool3_shoot(m, c, w, n_jobs, phase == k3Trial, T.tp.EaR_c, tab);
+    if (phase == k3Start) {
+      st.f = evaluate3_obj(m, c, st.N, w, X3, EQ3);
+      phase = k3Check;
+    } else if (phase == k3Trial) {
+      st.ft = evaluate3_obj(m, c, st.N, w, XT3, TQ3);
+      const int r = sqp3_trial_result(c, w, st);
+      if (r == 0) {
+        phase = k3Check;
+      } else if (r == 1) {
+        nmpc3_apply(m, c, w, T, st.info);
+        phase = k3Sample;
+      }
+    }
   }
-  out.phi = phi / (double)(K + 1);
-  return out;
 }
 
 }  // namespace mc

@@ -115,7 +115,8 @@ WORKLOADS = {
     # paper-scale FP64 study with the controller on the plant's own model
     "cstr_30k_x240_N20_fp64_nx3": dict(
         model=model(240, dTin_step=5.0),
-        nmpc=dict(nmpc(20), nx_model=3, schedule="static"), pi=pi(), n_traj=30000, seed=SEED),
+        nmpc=dict(nmpc(20), nx_model=3, schedule="persistent"), pi=pi(), n_traj=30000,
+        seed=SEED),
     # uneven batches: 262,144 trajectories, 120 steps, horizon uniform on 10..40 and
     # SQP iteration limit uniform on 5..30 per trajectory, persistent schedule
     "cstr_262k_x120_N10to40_uneven": dict(

@@ -74,10 +74,31 @@ def test_three_state_and_one_state_controllers_agree_roughly():
     assert abs(phi3.mean() / phi1.mean() - 1.0) < 0.05
 
 
+def test_persistent_schedule_is_bit_identical_to_static():
+    """The persistent schedule (per-lane phases, a shooting pool per round)
+    runs the same arithmetic per trajectory as the static one; with
+    threads_per_sm = 1 fewer lanes than trajectories exercise the queue."""
+    w = W.get(WL)
+    m = dict(w["model"], n_steps=12)
+    out = {}
+    for sched, tps in (("static", 0), ("persistent", 0), ("persistent", 1)):
+        h = mc.MonteCarlo(m, dict(w["nmpc"], schedule=sched, threads_per_sm=tps), 200,
+                          w["seed"])
+        h.run()
+        h.sync()
+        out[(sched, tps)] = (h.phi(), h.counters())
+        h.close()
+    ref_phi, ref_cnt = out[("static", 0)]
+    for key in (("persistent", 0), ("persistent", 1)):
+        phi, cnt = out[key]
+        assert np.array_equal(phi, ref_phi), key
+        for k in ref_cnt:
+            assert np.array_equal(cnt[k], ref_cnt[k]), (key, k)
+
+
 def test_three_state_validation():
     w = W.get(WL)
     base = w["nmpc"]
-    for bad in (dict(precision="mixed"), dict(schedule="persistent"), dict(qp_solver="ipm"),
-                dict(nx_model=2)):
+    for bad in (dict(precision="mixed"), dict(qp_solver="ipm"), dict(nx_model=2)):
         with pytest.raises(mc.McError):
             mc.MonteCarlo(w["model"], dict(base, **bad), 4, w["seed"])
