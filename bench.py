@@ -46,12 +46,13 @@ W_EXP, W_DIV, W_LOG, W_SQRT, W_SINCOS = 16.9, 5.6, 29.3, 8.6, 26.7
 # per unit, from the kernel source (one state, one input):
 OPS_MODEL1 = 15 + W_EXP + W_DIV               # f, df/dx, df/dF of the one-state model
 OPS_RK4_SENS = 4 * OPS_MODEL1 + 29            # one RK4 step with forward sensitivities
-OPS_INTERVAL_EXTRA = 10                       # F/V, B = Fconv b, g_k, q_k, objective term
+OPS_INTERVAL_EXTRA = 12                       # F/V, (F sigma_T)^2, B = Fconv b, g_k, q_k, objective
+OPS_COV_STEP = 15                             # CD-EKF covariance on an RK4 step of interval 0
 OPS_QP_STAGE = 24 + W_DIV                     # active-set iteration, per stage
 OPS_SQP_STAGE = 45 + 2 * W_DIV                # gradient, KKT test, block BFGS, merit
 OPS_ACCEPT_STAGE = 15 + W_DIV                 # multiplier step, gradients, copy
 OPS_TRIAL_STAGE = 6                           # trial point and its merit sum
-OPS_EKF = 5 * (4 * (19 + W_EXP + W_DIV) + 8) + 12 + W_DIV    # predict (N_c = 5) + filter
+OPS_EKF = 12 + W_DIV                          # filter (the prediction rides on interval 0)
 OPS_EM = 38 + W_EXP + W_DIV - 5.6 + 12 + 2 * (8 + W_LOG + W_SQRT + W_SINCOS)  # substep
 PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
 
@@ -70,6 +71,7 @@ def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st):
     per_interval = nrk * OPS_RK4_SENS + OPS_INTERVAL_EXTRA
     first_evals = n_traj * N + (st["n_ocp"] - n_traj) * min(N, 2)   # warm starts reuse N-2
     ops = (first_evals + st["ls_trials"] * N) * per_interval
+    ops += (st["n_ocp"] + st["ls_trials"]) * nrk * OPS_COV_STEP   # interval 0 of each evaluation
     ops += st["qp_iters"] * N * OPS_QP_STAGE
     ops += st["sqp_iters"] * N * (OPS_SQP_STAGE + OPS_ACCEPT_STAGE)
     ops += st["ls_trials"] * N * OPS_TRIAL_STAGE

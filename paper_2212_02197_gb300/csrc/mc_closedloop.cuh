@@ -145,12 +145,13 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
   }
   const double y = cT + m.meas_sd * (double)meas_noise<R>(m, T.j, (uint32_t)T.i);
   if (T.i > 0) {
-    R xr = (R)T.xhat, Pr = (R)T.P;
-    ekf_predict<R>(m, (R)T.tp.EaR_c, c.n_rk4, (R)T.F_prev, xr, Pr);
-    T.xhat = (double)xr;
-    T.P = (double)Pr;
+    // the CD-EKF prediction from x-hat_{i-1|i-1}, P_{i-1|i-1} under the applied
+    // input: the last OCP's interval-0 shooting at its final iterate carried it
+    T.xhat = w(EPR, 0);
+    T.P = w(EPR, 1);
   }
   ekf_filter(m, y, T.xhat, T.P);
+  w(PIN, 0) = T.P;
   for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(T.i + k) * m.Ts);
   if (c.Ru != 0.0)
     for (int k = 1; k <= N; ++k) w(VB, k) = Fss(m, T.tp.EaR_c, w(ZB, k)) / c.Fconv;
@@ -304,11 +305,17 @@ __device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, 
     const int aa = trial ? TA : EA, ba = trial ? TB : EB, ga = trial ? TG : EG;
     const Ws wo{w.p + (o - lane), w.ld, w.N1};
     const double xk = (k == 0) ? wo(X, 0) : wo(xa, k);
-    double A, B, g;
-    shoot_interval<R>(m, c, tab.EaR[o], xk, wo(ua, k), wo(xa, k + 1), xs, ixs, A, B, g);
+    double A, B, g, xpr, Ppr;
+    shoot_interval<R>(m, c, tab.EaR[o], xk, wo(ua, k), wo(xa, k + 1), xs, ixs, A, B, g, k == 0,
+                      wo(PIN, 0), xpr, Ppr);
     wo(aa, k) = A;
     wo(ba, k) = B;
     wo(ga, k) = g;
+    if (k == 0) {
+      const int pa = trial ? TPR : EPR;
+      wo(pa, 0) = xpr;
+      wo(pa, 1) = Ppr;
+    }
   }
   __syncwarp();  // the shot intervals are visible to their owners
 }

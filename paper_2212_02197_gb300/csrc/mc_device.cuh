@@ -263,13 +263,20 @@ __device__ __forceinline__ void model1(const DevModel& m, R EaR, R x, R F, R& f,
 // flow F = v Fconv, and the forward sensitivities a = dx/dx0, B = dx/dv.
 // The RK4 stages propagate b = dx/dF, whose forcing is df/dF itself; B is
 // Fconv b, formed once at the end.
+// With cov, the same stages also carry the CD-EKF covariance of Eq.
+// (predictionEquations), dP/dt = 2 (df/dx) P + (F sigma_T)^2, from P0 into
+// P1: xF and P1 are then the CD-EKF prediction, RK4 on (x, P) over one sample
+// from (x0, P0) under this input.
 template <class R, bool kSens>
 __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4, R Ts, R x0,
-                                             R v, R Fconv, R& xF, R& A, R& B) {
+                                             R v, R Fconv, R& xF, R& A, R& B,
+                                             bool cov = false, R P0 = 0, R* P1 = nullptr) {
   const R h = Ts / (R)n_rk4;
   const R hh = (R)0.5 * h, h6 = h / (R)6;
   const R F = v * Fconv;
-  R x = x0, a = 1, b = 0;
+  const R sq = F * (R)m.sigma[2];
+  const R q = sq * sq;
+  R x = x0, a = 1, b = 0, Ps = P0;
   for (int s = 0; s < n_rk4; ++s) {
     R f1, fx1, fF1, f2, fx2, fF2, f3, fx3, fF3, f4, fx4, fF4;
     model1<R>(m, EaR, x, F, f1, fx1, fF1);
@@ -287,38 +294,19 @@ __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4
       a = a + h6 * (a1 + (R)2 * a2 + (R)2 * a3 + a4);
       b = b + h6 * (b1 + (R)2 * b2 + (R)2 * b3 + b4);
     }
+    if (cov) {
+      const R p1 = (R)2 * fx1 * Ps + q;
+      const R p2 = (R)2 * fx2 * (Ps + hh * p1) + q;
+      const R p3 = (R)2 * fx3 * (Ps + hh * p2) + q;
+      const R p4 = (R)2 * fx4 * (Ps + h * p3) + q;
+      Ps = Ps + h6 * (p1 + (R)2 * p2 + (R)2 * p3 + p4);
+    }
     x = x + h6 * (f1 + (R)2 * f2 + (R)2 * f3 + f4);
   }
   xF = x;
   A = a;
   B = kSens ? b * Fconv : b;
-}
-
-// CD-EKF prediction, Eq. (predictionEquations): RK4 on (x, P) with
-// dP/dt = 2 (df/dx) P + (F sigma_T)^2 over one sample time.
-template <class R>
-__device__ __forceinline__ void ekf_predict(const DevModel& m, R EaR, int n_rk4, R F, R& x,
-                                            R& P) {
-  const R h = (R)m.Ts / (R)n_rk4;
-  const R hh = (R)0.5 * h, h6 = h / (R)6;
-  const R sq = F * (R)m.sigma[2];
-  const R q = sq * sq;
-  R xs = x, Ps = P;
-  for (int s = 0; s < n_rk4; ++s) {
-    R f1, A1, f2, A2, f3, A3, f4, A4, d;
-    model1<R>(m, EaR, xs, F, f1, A1, d);
-    const R p1 = (R)2 * A1 * Ps + q;
-    model1<R>(m, EaR, xs + hh * f1, F, f2, A2, d);
-    const R p2 = (R)2 * A2 * (Ps + hh * p1) + q;
-    model1<R>(m, EaR, xs + hh * f2, F, f3, A3, d);
-    const R p3 = (R)2 * A3 * (Ps + hh * p2) + q;
-    model1<R>(m, EaR, xs + h * f3, F, f4, A4, d);
-    const R p4 = (R)2 * A4 * (Ps + h * p3) + q;
-    xs = xs + h6 * (f1 + (R)2 * f2 + (R)2 * f3 + f4);
-    Ps = Ps + h6 * (p1 + (R)2 * p2 + (R)2 * p3 + p4);
-  }
-  x = xs;
-  P = Ps;
+  if (cov) *P1 = Ps;
 }
 
 // CD-EKF filtering with the Joseph-form covariance, Eq. (Josph); always FP64.

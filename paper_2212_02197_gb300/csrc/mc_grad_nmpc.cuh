@@ -284,12 +284,14 @@ __device__ TrajOut traj_nmpc_grad(const DevModel& m, const DevCtrl& c, uint32_t 
   double dxh[3] = {0, 0, 0}, dPh[3] = {0, 0, 0}, dFp[3] = {0, 0, 0}, dph[3] = {0, 0, 0};
   const int K = m.n_steps;
   for (;;) {
-    // tangents of this sample's Phi term, measurement and CD-EKF; the values
-    // they start from are the ones nmpc_sample uses
+    // tangents of this sample's Phi term, measurement and CD-EKF, at the values
+    // nmpc_sample starts from: the prediction the last OCP's interval-0
+    // shooting carried, read before the next OCP's evaluation overwrites it
     const double t_i = m.t0 + (double)T.i * m.Ts;
     const double cT = T.n[2] / m.V;
     const double xh0 = T.xhat, Ph0 = T.P, Fp = T.F_prev;
     const int i = T.i;
+    const double xp = (i > 0) ? w(EPR, 0) : xh0, Pp = (i > 0) ? w(EPR, 1) : Ph0;
     if (isfinite(cT)) {
       const double zi = zbar(m, t_i);
 #pragma unroll
@@ -301,11 +303,7 @@ __device__ TrajOut traj_nmpc_grad(const DevModel& m, const DevCtrl& c, uint32_t 
     double dy[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) dy[d] = dn[d][2] / m.V;
-    double xp = xh0, Pp = Ph0;
-    if (i > 0) {
-      ekf_predict_tan(m, T.tp.EaR_c, c.n_rk4, Fp, xh0, Ph0, dFp, dxh, dPh);
-      ekf_predict<double>(m, T.tp.EaR_c, c.n_rk4, Fp, xp, Pp);
-    }
+    if (i > 0) ekf_predict_tan(m, T.tp.EaR_c, c.n_rk4, Fp, xh0, Ph0, dFp, dxh, dPh);
     const double y = cT + m.meas_sd * meas_noise<double>(m, T.j, (uint32_t)i);
     ekf_filter_tan(m, y, xp, Pp, dy, dxh, dPh);
     // the OCP

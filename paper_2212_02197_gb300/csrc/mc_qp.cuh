@@ -35,6 +35,8 @@ enum Arr : int {
   TL, TU, ZL, ZU, DUA, RIR, RSB,  // IPM slacks, duals, affine du, 1/Rbar, Sbar
   DXS, DMS,                       // IPM step in dx and mu
   VB,                             // steady-state inputs vbar_k of the set-points (R_u term)
+  PIN, TPR, EPR,                  // P_{i|i} (row 0); the CD-EKF prediction (x, P in rows 0,
+                                  // 1) carried by the interval-0 shooting: trial, current
   kNArr
 };
 

@@ -40,16 +40,21 @@ struct SqpState {
 // g_k = F_k - x_{k+1}.  Not inlined: the loop of evaluate and the persistent
 // schedule's shooting pool (any lane integrating any lane's interval) run this
 // one compiled body, so both give the same bits.
+// With cov (interval 0), the same RK4 stages also give the CD-EKF prediction
+// of the next sample from (x_0, P0) under this input: xpr = F_0 in K L and Ppr.
 template <class R>
 __device__ __noinline__ void shoot_interval(const DevModel& m, const DevCtrl& c, double EaR,
                                             double xk, double uk, double xn, double xs,
-                                            double ixs, double& A, double& B, double& g) {
-  R Fn, a, b;
+                                            double ixs, double& A, double& B, double& g,
+                                            bool cov, double P0, double& xpr, double& Ppr) {
+  R Fn, a, b, P1 = 0;
   rk4_interval<R, true>(m, (R)EaR, c.n_rk4, (R)m.Ts, (R)(xk * xs), (R)uk, (R)c.Fconv, Fn, a,
-                        b);
+                        b, cov, (R)P0, &P1);
   A = (double)a;
   B = (double)b * ixs;
   g = (double)Fn * ixs - xn;
+  xpr = (double)Fn;
+  Ppr = (double)P1;
 }
 
 // Which intervals evaluate integrates.
@@ -78,14 +83,20 @@ __device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, dou
   const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
   double f = 0.0;
   double xk = w(X, 0);
+  const int pr_arr = (a_arr == TA) ? TPR : EPR;
   for (int k = 0; k < N; ++k) {
     const double xn = w(x_arr, k + 1);
     if (rk_mode == kRkAll || (rk_mode == kRkEnds && (k == 0 || k == N - 1))) {
-      double A, B, g;
-      shoot_interval<R>(m, c, EaR, xk, w(u_arr, k), xn, xs, ixs, A, B, g);
+      double A, B, g, xpr, Ppr;
+      shoot_interval<R>(m, c, EaR, xk, w(u_arr, k), xn, xs, ixs, A, B, g, k == 0, w(PIN, 0),
+                        xpr, Ppr);
       w(a_arr, k) = A;
       w(b_arr, k) = B;
       w(g_arr, k) = g;
+      if (k == 0) {
+        w(pr_arr, 0) = xpr;
+        w(pr_arr, 1) = Ppr;
+      }
     }
     const double dz = xn * xs * m.iV - w(ZB, k + 1);
     f += c.Qz * dz * dz * m.Ts;
@@ -361,6 +372,8 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
     w(EG, k) = w(TG, k);
     w(EQ, k + 1) = w(TQ, k + 1);
   }
+  w(EPR, 0) = w(TPR, 0);
+  w(EPR, 1) = w(TPR, 1);
   s.f = s.ft;
   s.l++;
   return 0;
@@ -395,6 +408,7 @@ __device__ __noinline__ SqpInfo sqp_solve(const DevModel& m, const DevCtrl& c, d
                                           double x0, const Ws& w, bool shifted_eval = false,
                                           int N = 0, int max_it = -1) {
   SqpState s;
+  w(PIN, 0) = 0.0;  // no filter here: the prediction the shooting carries is unused
   sqp_start<R>(m, c, EaR, x0, w, N > 0 ? N : c.N, max_it >= 0 ? max_it : c.sqp_max_it,
                shifted_eval, s);
   while (!sqp_check<R>(c, w, s)) {
