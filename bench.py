@@ -58,10 +58,10 @@ PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 G
 
 # DRAM bytes (read + write) of k_nmpc_persist<double> per control step of the
 # 30,000-trajectory FP64 study, from one ncu capture of a 60-step case of it
-# (dram__bytes_read.sum 60.37 GB + dram__bytes_write.sum 77.58 GB).  A full
+# (dram__bytes_read.sum 62.50 GB + dram__bytes_write.sum 78.70 GB).  A full
 # launch is scaled by its steps and trajectories.
 TRAFFIC_WORKLOAD = "cstr_30k_x240_N20_fp64"
-TRAFFIC_BYTES_PER_STEP_30K = (60368409344 + 77580626688) / 60
+TRAFFIC_BYTES_PER_STEP_30K = (62495836160 + 78695064320) / 60
 
 
 def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st):
