@@ -130,9 +130,13 @@ typedef struct {
 
 typedef enum {
   MC_SCHED_STATIC = 0,    /* one thread per trajectory, OCPs in lock-step      */
-  MC_SCHED_PERSISTENT = 1 /* per-lane state machine, shared line-search
-                             shooting, trajectories taken from a queue (longest
-                             horizons first when horizons differ)             */
+  MC_SCHED_PERSISTENT = 1 /* per-lane state machine; each round the warp
+                             shoots all pending intervals (trial points and
+                             OCP starts) as one pool and draws the plant noise
+                             of the OCPs it starts; trajectories taken from a
+                             queue (longest horizons first when horizons
+                             differ).  Same results as the static schedule,
+                             bit for bit                                       */
 } mc_schedule;
 
 /* Reduced results of the last run (Table II and Fig. 3 of Sec. VII). */
@@ -273,7 +277,8 @@ mc_status mc_set_nmpc_weights(mc_handle* h, double Qz, double Ru, double Qn);
  * Writes Phi_j, the counters (counter 7 also counts OCPs whose reduced
  * Hessian was not positive definite; their input tangent is 0) and
  * dPhi_j/d(Q_z, R_u, Q_n) per trajectory (read with mc_grad_mean,
- * mc_copy_grad).  Static schedule.  MC_EINVAL for a PI, mixed-precision or
+ * mc_copy_grad).  Runs on the static schedule whatever the handle's.
+ * MC_EINVAL for a PI, mixed-precision or
  * three-state handle or a bad range; MC_ENOMEM if the gradient buffers
  * cannot be had. */
 mc_status mc_nmpc_grad(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream);
