@@ -252,6 +252,26 @@ def test_ekf_predict_linear_closed_form():
             assert Pp == pytest.approx(Pe, rel=bound)
 
 
+def test_ekf_prediction_state_is_the_one_interval_shooting():
+    """The state part of the CD-EKF prediction (Eq. (predictionEquations): RK4
+    on x' = f(x, F) over one sample) and the OCP's shooting of one interval
+    (Eq. (OCP_NLP): RK4 on the same model, the same N_c steps, from the same x
+    under the same flow F = v F_conv) are one integration.  The GPU path
+    therefore takes the prediction from the interval-0 shooting of the last
+    OCP's final iterate; here the oracle's two routines agree to rounding,
+    also far from steady state and near the unstable branch."""
+    m = dict(M)
+    c = W.nmpc()
+    Fconv = c["u_scale"] / 60000.0
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        x = V * rng.uniform(270.0, 360.0)
+        v = rng.uniform(0.0, 1.0)
+        xp, _ = oracle.ekf_predict(m, c["n_rk4"], v * Fconv, x, 1e-3)
+        xF, _, _ = oracle.rk4_interval(m, c["n_rk4"], m["Ts"], x, v, Fconv)
+        assert xp == pytest.approx(xF, rel=1e-14, abs=0), (x, v)
+
+
 def test_ekf_filter_is_bayes_posterior_and_joseph_equals_short():
     """For a linear measurement y = x/V + v the filtered pair is the Gaussian
     posterior: precision 1/P + C^2/R, mean (x/P + C y/R) / precision, C = 1/V."""
