@@ -26,6 +26,18 @@ MAX_SP = 16
 MAX_N = 64
 
 
+def compile_sources(src_dir: str, out: str) -> str:
+    """Compile the oracle's C sources found in ``src_dir`` into the shared
+    library ``out`` (the flags of ``build``)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+           "-Wall", "-Wno-unused-function", "-o", tmp]
+    cmd += [os.path.join(src_dir, s) for s in _SRC] + ["-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` with gcc.
 
@@ -36,13 +48,12 @@ def build(force: bool = False) -> str:
         so_t = os.path.getmtime(_SO)
         if all(os.path.getmtime(s) <= so_t for s in srcs):
             return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-Wall", "-Wno-unused-function", "-o", tmp]
-    cmd += [os.path.join(_HERE, s) for s in _SRC] + ["-lm", "-lpthread"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    return compile_sources(_HERE, _SO)
+
+
+def sources() -> list[str]:
+    """Paths of the oracle's C sources and header."""
+    return [os.path.join(_HERE, s) for s in _SRC] + [os.path.join(_HERE, "oracle.h")]
 
 
 class Model(C.Structure):
@@ -87,8 +98,13 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_SO)
+            # MC_ORACLE_LIB: a library built from altered sources, for the
+            # tests that check the pins fail on planted mistakes
+            path = os.environ.get("MC_ORACLE_LIB")
+            if not path:
+                build()
+                path = _SO
+            L = C.CDLL(path)
             u32p = C.POINTER(C.c_uint32)
             L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.or_uniform52.argtypes = [C.c_uint32, C.c_uint32]
