@@ -73,6 +73,26 @@ MUTANTS = [
      "K[IU(k) * n + IX(k)] += -lam[k] * Fxu[k];",
      "K[IU(k) * n + IX(k)] += 0.0 * Fxu[k];",
      "test_oracle_sqp.py", "ocp_sensitivity"),
+    ("Box-Muller: angle of pi instead of 2 pi", "or_random.c",
+     "const double ang = 2.0 * M_PI * u2;",
+     "const double ang = M_PI * u2;",
+     "test_oracle_random.py", "box_muller"),
+    ("set-point schedule: strict comparison", "or_model.c",
+     "if (t >= m->sp_time[s]) z = m->sp_value[s];",
+     "if (t > m->sp_time[s]) z = m->sp_value[s];",
+     "test_oracle_model.py", "zbar"),
+    ("trajectory parameters: lognormal E_a/R without its spread", "or_random.c",
+     "*EaR_j = (m->Ea_logsd != 0.0) ? m->EaR * exp(m->Ea_logsd * z[0]) : m->EaR;",
+     "*EaR_j = (m->Ea_logsd != 0.0) ? m->EaR * exp(0.5 * m->Ea_logsd * z[0]) : m->EaR;",
+     "test_oracle_closedloop.py", "trajectory_parameters"),
+    ("three-state drift: Jacobian misses the dilution term", "or_nmpc3.c",
+     "for (int q = 0; q < 3; ++q) J[p * 3 + q] = (p == q ? -F / V : 0.0) + S[p] * drv[q];",
+     "for (int q = 0; q < 3; ++q) J[p * 3 + q] = S[p] * drv[q];",
+     "test_oracle_nmpc3.py", "drift3_is_the_plant_drift"),
+    ("PI gradient: complex-step path with the anti-windup sign flipped", "or_grad.c",
+     "Ihat = Ii + m->Ts * kaw * (uhat - u);",
+     "Ihat = Ii + m->Ts * kaw * (u - uhat);",
+     "test_oracle_grad.py", "real_part or richardson"),
 ]
 
 
