@@ -64,6 +64,29 @@ def test_closed_loop_matches_oracle():
     assert abs(cnt["sqp_iters"].sum() / ref["sqp_iters"].sum() - 1.0) < 0.02
 
 
+def test_full_study_sampled():
+    """The full three-state study (30,000 trajectories, 240 steps, the
+    workload's persistent schedule) in one launch; 48 trajectories spread over
+    the index range against the oracle, with the tolerances of the 60-step
+    test (OCPs stop at the scaled KKT tolerance 1e-5, Sec. IV)."""
+    w = W.get(WL)
+    n = w["n_traj"]
+    phi, cnt, st = _run(w["model"], w["nmpc"], n, w["seed"])
+    assert st["n_traj"] == n and st["n_nonfinite"] == 0
+    assert st["n_ocp"] == n * w["model"]["n_steps"]
+    assert st["n_ocp_failed"] <= 1e-3 * st["n_ocp"]
+    sample = np.unique(np.linspace(0, n - 1, 48).astype(int))
+    refs = [oracle.run(w["model"], w["nmpc"], w["seed"], int(j), int(j) + 1, threads=1)
+            for j in sample]
+    ref_phi = np.concatenate([r["phi"] for r in refs])
+    ref_fail = np.concatenate([r["n_ocp_failed"] for r in refs])
+    rel = np.abs(phi[sample] - ref_phi) / np.abs(ref_phi)
+    hit = (ref_fail > 0) | (cnt["n_ocp_failed"][sample] > 0)
+    assert np.all(rel[~hit] <= 1e-5), (rel[~hit].max(), sample[np.argmax(np.where(hit, 0, rel))])
+    assert np.mean(rel[~hit] <= 1e-6) >= 0.9, np.sort(rel[~hit])[-8:]
+    assert np.all(rel[hit] <= 1e-3)
+
+
 def test_three_state_and_one_state_controllers_agree_roughly():
     """Both control the same plant; with the plant near the reaction-invariant
     manifold they track alike (mean Phi within 5 %)."""
