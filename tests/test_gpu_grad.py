@@ -216,6 +216,35 @@ def test_nmpc_grad_matches_oracle_per_trajectory():
     assert st["n_nonfinite"] == 0
 
 
+def test_nmpc_grad_full_study_sampled():
+    """The NMPC-weight gradient of the full 30,000-trajectory, 240-step study
+    (R_u = 0.2, Q_n = 1) in one launch, as the benchmark times it; 24
+    trajectories across the index range against the oracle's complex-step
+    derivative, with the per-trajectory tolerances of the 40-step test."""
+    w = W.get(WL)
+    n = w["n_traj"]
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+    h = mc.MonteCarlo(w["model"], c, n, w["seed"])
+    h.nmpc_grad()
+    st = h.stats(timeout_ms=1800000)
+    phi, g, cnt = h.phi(), h.grad(), h.counters()
+    h.close()
+    assert st["n_traj"] == n and st["n_nonfinite"] == 0
+    sample = np.unique(np.linspace(0, n - 1, 24).astype(int))
+    rphi, rg, fails = [], [], []
+    for j in sample:
+        p_, g_, f_ = oracle.nmpc_grad(w["model"], c, w["seed"], int(j), int(j) + 1)
+        rphi.append(p_[0]), rg.append(g_[0]), fails.append(f_[0])
+    rphi, rg, fails = np.array(rphi), np.array(rg), np.array(fails)
+    ok = (cnt["n_ocp_failed"][sample] == 0) & (fails == 0)
+    assert ok.sum() >= 0.75 * len(sample)
+    np.testing.assert_allclose(phi[sample][ok], rphi[ok], rtol=1e-6)
+    gs = g[sample][ok]
+    scale = np.abs(rg[ok]).max(axis=0)
+    err = np.abs(gs - rg[ok]) / (np.abs(rg[ok]) + 1e-3 * scale)
+    assert err.max() < 1e-3, err.max()
+
+
 def test_nmpc_grad_phi_equals_the_static_run():
     w = W.get(WN)
     m = dict(w["model"], n_steps=40)

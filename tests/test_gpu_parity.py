@@ -428,6 +428,26 @@ def test_model_mismatch_matches_oracle(kind):
     hk.close()
 
 
+def test_model_mismatch_full_study_sampled():
+    """The full mismatch study (30,000 trajectories, 240 steps, lognormal
+    E_a/R in the plant only) in one launch of the benchmark's schedule; 48
+    trajectories across the index range against the oracle."""
+    w = W.get("cstr_30k_x240_N20_fp64_mismatch")
+    n = w["n_traj"]
+    h = mc.MonteCarlo(w["model"], w["nmpc"], n, w["seed"])
+    h.run()
+    st = h.stats(timeout_ms=1800000)
+    phi, cnt = h.phi(), h.counters()
+    h.close()
+    assert st["n_traj"] == n and st["n_nonfinite"] == 0
+    assert st["n_ocp"] == n * w["model"]["n_steps"]
+    sample = np.unique(np.linspace(0, n - 1, 48).astype(int))
+    refs = [oracle.run(w["model"], w["nmpc"], w["seed"], int(j), int(j) + 1, threads=1)
+            for j in sample]
+    ref = {k: np.concatenate([r[k] for r in refs]) for k in refs[0]}
+    compare_phi(phi[sample], ref, {k: v[sample] for k, v in cnt.items()}, 1e-6)
+
+
 # ------------------------------------------------------------------ schedules
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
