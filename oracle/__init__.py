@@ -89,6 +89,25 @@ class SqpInfo(C.Structure):
                 ("kkt_grad", C.c_double), ("kkt_eq", C.c_double), ("f", C.c_double)]
 
 
+TRACE_MAX_TRIALS = 64
+
+
+class SqpTraceRow(C.Structure):
+    _fields_ = [("l", C.c_int32), ("reset", C.c_int32), ("n_trials", C.c_int32),
+                ("accepted", C.c_int32), ("stop", C.c_int32), ("pad0", C.c_int32),
+                ("s_d", C.c_double), ("kkt_grad_raw", C.c_double), ("kkt_grad", C.c_double),
+                ("kkt_eq", C.c_double), ("f", C.c_double), ("T0", C.c_double),
+                ("DT0", C.c_double), ("lam", C.c_double * MAX_N), ("pil", C.c_double * MAX_N),
+                ("piu", C.c_double * MAX_N), ("g", C.c_double * MAX_N),
+                ("q", C.c_double * (MAX_N + 1)), ("r", C.c_double * MAX_N),
+                ("A", C.c_double * MAX_N), ("B", C.c_double * MAX_N),
+                ("du", C.c_double * MAX_N), ("dx", C.c_double * (MAX_N + 1)),
+                ("mu", C.c_double * MAX_N), ("sigma", C.c_double * MAX_N),
+                ("alpha", C.c_double * TRACE_MAX_TRIALS),
+                ("f_trial", C.c_double * TRACE_MAX_TRIALS),
+                ("pen_trial", C.c_double * TRACE_MAX_TRIALS)]
+
+
 _lib = None
 _lock = threading.Lock()
 _dp = C.POINTER(C.c_double)
@@ -134,6 +153,13 @@ def lib():
             L.or_sqp.argtypes = [C.POINTER(Model), C.POINTER(Ctrl), C.c_double, C.c_double,
                                  _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(SqpInfo)]
             L.or_sqp.restype = C.c_int
+            L.or_sqp_traced.argtypes = ([C.POINTER(Model), C.POINTER(Ctrl), C.c_double,
+                                         C.c_double] + [_dp] * 6 +
+                                        [C.POINTER(SqpInfo), C.POINTER(SqpTraceRow), C.c_int,
+                                         C.POINTER(C.c_int)])
+            L.or_sqp_traced.restype = C.c_int
+            L.or_bfgs_update_blocks.argtypes = [C.c_int] + [_dp] * 5
+            L.or_bfgs_update_blocks.restype = C.c_int
             L.or_bfgs_block.argtypes = [C.c_int, _dp, _dp, _dp]
             L.or_traj_horizon.argtypes = [C.POINTER(Ctrl), C.c_uint64, C.c_int64,
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -290,6 +316,57 @@ def sqp(model: dict, ctrl: dict, EaR: float, x0: float, zbar, u, x, lam=None, pi
              _p(piu), C.byref(info))
     d = {f: getattr(info, f) for f, _ in SqpInfo._fields_ if f != "pad0"}
     return u, x, lam, pil, piu, d
+
+
+def sqp_traced(model: dict, ctrl: dict, EaR: float, x0: float, zbar, u, x, lam=None,
+               pil=None, piu=None, max_rows: int = 256):
+    """One OCP as ``sqp``, plus one trace row per SQP iteration: a list of dicts
+    with the quantities each step of Sec. IV saw (arrays cut to N or N + 1)."""
+    L = lib()
+    m, c = make_model(model), make_ctrl(ctrl)
+    N = c.N
+    zb = np.ascontiguousarray(zbar, dtype=np.float64)
+    u = np.array(u, dtype=np.float64)
+    x = np.array(x, dtype=np.float64)
+    lam = np.zeros(N) if lam is None else np.array(lam, dtype=np.float64)
+    pil = np.zeros(N) if pil is None else np.array(pil, dtype=np.float64)
+    piu = np.zeros(N) if piu is None else np.array(piu, dtype=np.float64)
+    info = SqpInfo()
+    rows = (SqpTraceRow * max_rows)()
+    nr = C.c_int(0)
+    L.or_sqp_traced(C.byref(m), C.byref(c), EaR, x0, _p(zb), _p(u), _p(x), _p(lam), _p(pil),
+                    _p(piu), C.byref(info), rows, max_rows, C.byref(nr))
+    d = {f: getattr(info, f) for f, _ in SqpInfo._fields_ if f != "pad0"}
+    out = []
+    for i in range(nr.value):
+        r = rows[i]
+        row = {}
+        for f, t in SqpTraceRow._fields_:
+            v = getattr(r, f)
+            if f == "pad0":
+                continue
+            if f in ("alpha", "f_trial", "pen_trial"):
+                row[f] = np.array(v[: r.n_trials])
+            elif f in ("q", "dx"):
+                row[f] = np.array(v[: N + 1])
+            elif hasattr(v, "__len__"):
+                row[f] = np.array(v[:N])
+            else:
+                row[f] = v
+        out.append(row)
+    return u, x, lam, pil, piu, d, out
+
+
+def bfgs_update_blocks(W, s_u, s_x, y_u, y_x):
+    """The block-BFGS step with the reset rule on N + 1 packed blocks W
+    ((N + 1) x 3); returns (updated W, reset flag)."""
+    W = np.array(W, dtype=np.float64).reshape(-1, 3).copy()
+    N = W.shape[0] - 1
+    s_u, y_u = (np.ascontiguousarray(a, dtype=np.float64) for a in (s_u, y_u))
+    s_x, y_x = (np.ascontiguousarray(a, dtype=np.float64) for a in (s_x, y_x))
+    assert len(s_u) == N and len(y_u) == N and len(s_x) == N + 1 and len(y_x) == N + 1
+    reset = lib().or_bfgs_update_blocks(N, _p(W), _p(s_u), _p(s_x), _p(y_u), _p(y_x))
+    return W, reset
 
 
 def qp_solve(A, B, b, Wxx, Wxu, Wuu, q, r, lb, ub):

@@ -316,9 +316,43 @@ static int block_pd(int n, const double* w) {
   return (w[2] - w[1] * w[1] / w[0]) > 0.0;
 }
 
-int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
-           const double* zbar, double* u, double* x, double* lam, double* pil,
-           double* piu, or_sqp_info* info) {
+/* The block-BFGS step of Sec. IV-C on all N + 1 blocks (W[k] packed as above;
+ * block 0 = [u_0], block k = [x_k u_k], block N = [x_N]): the damped update of
+ * every block, then the reset of all blocks to the identity when any of them
+ * is not positive definite.  Returns 1 after a reset. */
+static int bfgs_update_blocks(int N, double (*Wb)[3], const double* s_u, const double* s_x,
+                              const double* y_u, const double* y_x) {
+  double s2[2], y2[2];
+  s2[0] = s_u[0]; y2[0] = y_u[0];
+  bfgs_block(1, Wb[0], s2, y2);
+  for (int k = 1; k < N; ++k) {
+    s2[0] = s_x[k]; s2[1] = s_u[k];
+    y2[0] = y_x[k]; y2[1] = y_u[k];
+    bfgs_block(2, Wb[k], s2, y2);
+  }
+  s2[0] = s_x[N]; y2[0] = y_x[N];
+  bfgs_block(1, Wb[N], s2, y2);
+  int pd = block_pd(1, Wb[0]) && block_pd(1, Wb[N]);
+  for (int k = 1; k < N; ++k) pd = pd && block_pd(2, Wb[k]);
+  if (!pd) {
+    for (int k = 0; k <= N; ++k) { Wb[k][0] = 1.0; Wb[k][1] = 0.0; Wb[k][2] = 1.0; }
+    return 1;
+  }
+  return 0;
+}
+
+/* exported for the tests: W holds the N + 1 packed blocks, 3 doubles each */
+int or_bfgs_update_blocks(int N, double* W, const double* s_u, const double* s_x,
+                          const double* y_u, const double* y_x) {
+  return bfgs_update_blocks(N, (double (*)[3])W, s_u, s_x, y_u, y_x);
+}
+
+/* The SQP; with rows != NULL each iteration that reaches the QP also writes
+ * one trace row (at most max_rows). */
+static int sqp_impl(const or_model* m, const or_ctrl* c, double EaR, double x0,
+                    const double* zbar, double* u, double* x, double* lam, double* pil,
+                    double* piu, or_sqp_info* info, or_sqp_trace_row* rows, int max_rows,
+                    int* n_rows) {
   const int N = c->N;
   const double Fconv = c->u_scale / 60000.0;      /* OCP unit -> L/s */
   const double umin = c->u_min / c->u_scale;      /* bounds in OCP units */
@@ -344,27 +378,19 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
   evaluate(m, c, EaR, Fconv, x0, zbar, u, x, &ev);
 
   int l = 0, nqp = 0;
+  if (n_rows) *n_rows = 0;
   for (;; ++l) {
+    int reset = 0;
     if (l > 0) {
       /* damped block BFGS with s = xi^[l] - xi^[l-1],
        * y = grad L(xi^[l], .) - grad L(xi^[l-1], .), both at the new multipliers */
       grad_lagrangian(N, &ev, lam, pil, piu, gu, gx);
-      double s2[2], y2[2];
-      s2[0] = s_u[0]; y2[0] = gu[0] - gu_old[0];
-      bfgs_block(1, Wb[0], s2, y2);
-      for (int k = 1; k < N; ++k) {
-        s2[0] = s_x[k]; s2[1] = s_u[k];
-        y2[0] = gx[k] - gx_old[k]; y2[1] = gu[k] - gu_old[k];
-        bfgs_block(2, Wb[k], s2, y2);
-      }
-      s2[0] = s_x[N]; y2[0] = gx[N] - gx_old[N];
-      bfgs_block(1, Wb[N], s2, y2);
-      int pd = block_pd(1, Wb[0]) && block_pd(1, Wb[N]);
-      for (int k = 1; k < N; ++k) pd = pd && block_pd(2, Wb[k]);
-      if (!pd) {
-        for (int k = 0; k <= N; ++k) { Wb[k][0] = 1.0; Wb[k][1] = 0.0; Wb[k][2] = 1.0; }
-        info->n_hess_reset++;
-      }
+      double y_u[OR_MAX_N], y_x[OR_MAX_N + 1];
+      for (int k = 0; k < N; ++k) y_u[k] = gu[k] - gu_old[k];
+      y_x[0] = 0.0;
+      for (int k = 1; k <= N; ++k) y_x[k] = gx[k] - gx_old[k];
+      reset = bfgs_update_blocks(N, Wb, s_u, s_x, y_u, y_x);
+      info->n_hess_reset += reset;
     }
 
     /* scaled convergence test, Eq. (convergence) */
@@ -375,17 +401,43 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
     double kg = 0.0, ke = 0.0;
     for (int k = 0; k < N; ++k) kg = fmax(kg, fabs(gu[k]));
     for (int k = 1; k <= N; ++k) kg = fmax(kg, fabs(gx[k]));
+    const double kg_raw = kg;
     kg /= s_d;
     for (int k = 0; k < N; ++k) ke = fmax(ke, fabs(ev.g[k]));
     info->kkt_grad = kg;
     info->kkt_eq = ke;
     info->f = ev.f;
+    or_sqp_trace_row* tr = NULL;
+    if (rows && *n_rows < max_rows) {
+      tr = &rows[(*n_rows)++];
+      memset(tr, 0, sizeof(*tr));
+      tr->stop = -1;
+      tr->l = l;
+      tr->reset = reset;
+      tr->s_d = s_d;
+      tr->kkt_grad_raw = kg_raw;
+      tr->kkt_grad = kg;
+      tr->kkt_eq = ke;
+      tr->f = ev.f;
+      for (int k = 0; k < N; ++k) {
+        tr->lam[k] = lam[k];
+        tr->pil[k] = pil[k];
+        tr->piu[k] = piu[k];
+        tr->g[k] = ev.g[k];
+        tr->r[k] = ev.r[k];
+        tr->A[k] = ev.A[k];
+        tr->B[k] = ev.B[k];
+      }
+      for (int k = 0; k <= N; ++k) tr->q[k] = ev.q[k];
+    }
     if (kg <= c->sqp_tol && ke <= c->sqp_tol) {
       info->status = 0;
+      if (tr) tr->stop = 0;
       break;
     }
     if (l >= c->sqp_max_it) {
       info->status = 1;
+      if (tr) tr->stop = 1;
       break;
     }
 
@@ -415,6 +467,16 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
     for (int k = 1; k <= N; ++k) dfd += ev.q[k] * dx[k];
     const double T0 = ev.f + pen;
     const double DT0 = dfd - pen;
+    if (tr) {
+      tr->T0 = T0;
+      tr->DT0 = DT0;
+      for (int k = 0; k < N; ++k) {
+        tr->du[k] = du[k];
+        tr->mu[k] = mu[k];
+        tr->sigma[k] = sigma[k];
+      }
+      for (int k = 0; k <= N; ++k) tr->dx[k] = dx[k];
+    }
 
     /* backtracking on the Armijo condition */
     double alpha = 1.0;
@@ -432,12 +494,19 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
       info->ls_trials++;
       double pt = 0.0;
       for (int k = 0; k < N; ++k) pt += sigma[k] * fabs(ev_trial.g[k]);
+      if (tr && tr->n_trials < OR_TRACE_MAX_TRIALS) {
+        tr->alpha[tr->n_trials] = alpha;
+        tr->f_trial[tr->n_trials] = ev_trial.f;
+        tr->pen_trial[tr->n_trials] = pt;
+        tr->n_trials++;
+      }
       if (ev_trial.f + pt <= T0 + c1 * alpha * DT0) {
         accepted = 1;
         break;
       }
       alpha *= beta_ls;
     }
+    if (tr) tr->accepted = accepted;
     if (!accepted) {
       info->status = 2;
       break;
@@ -460,6 +529,21 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
   }
   info->iters = nqp;
   return info->status;
+}
+
+int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
+           const double* zbar, double* u, double* x, double* lam, double* pil,
+           double* piu, or_sqp_info* info) {
+  return sqp_impl(m, c, EaR, x0, zbar, u, x, lam, pil, piu, info, NULL, 0, NULL);
+}
+
+int or_sqp_traced(const or_model* m, const or_ctrl* c, double EaR, double x0,
+                  const double* zbar, double* u, double* x, double* lam, double* pil,
+                  double* piu, or_sqp_info* info, or_sqp_trace_row* rows, int max_rows,
+                  int* n_rows) {
+  int dummy = 0;
+  return sqp_impl(m, c, EaR, x0, zbar, u, x, lam, pil, piu, info, rows, max_rows,
+                  n_rows ? n_rows : &dummy);
 }
 
 /* ------------------------------------------------------------------------ */

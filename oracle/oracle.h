@@ -150,6 +150,55 @@ int or_sqp(const or_model* m, const or_ctrl* c, double EaR, double x0,
            const double* zbar /* zbar[k], k = 1..N */, double* u, double* x,
            double* lam, double* pil, double* piu, or_sqp_info* info);
 
+/* One row per SQP iteration l (Sec. IV): what the
+ * penalty update (Sec. IV-B), the Armijo backtracking (Eq. Armijo), the scaled
+ * convergence test (Eq. convergence) and the Hessian reset (Sec. IV-C) saw and
+ * decided, so that tests can check each decision against the paper's rules. */
+#define OR_TRACE_MAX_TRIALS 64
+typedef struct {
+  int32_t l;            /* iteration index                                    */
+  int32_t reset;        /* 1: the block update that opened this iteration
+                           found a block not positive definite and reset all */
+  int32_t n_trials;     /* merit evaluations of this line search              */
+  int32_t accepted;     /* 1: a trial point was accepted                      */
+  int32_t stop;         /* -1: the iteration went on to the QP; else the SQP
+                           stopped here with this status (0 converged,
+                           1 iteration limit)                                */
+  int32_t pad0;
+  double s_d;           /* scaling of the convergence test                    */
+  double kkt_grad_raw;  /* ||grad_xi L||_inf before the scaling               */
+  double kkt_grad;      /* the scaled value the test compared                 */
+  double kkt_eq;        /* ||g||_inf                                          */
+  double f;             /* objective at the iterate                           */
+  double T0, DT0;       /* merit T(0) and its directional derivative          */
+  double lam[OR_MAX_N], pil[OR_MAX_N], piu[OR_MAX_N];  /* multipliers at the
+                           iterate (the ones the convergence test used)      */
+  double g[OR_MAX_N];   /* constraint residuals g_k at the iterate            */
+  double q[OR_MAX_N + 1], r[OR_MAX_N];   /* objective gradient at the iterate */
+  double A[OR_MAX_N], B[OR_MAX_N];       /* shooting sensitivities there      */
+  double du[OR_MAX_N], dx[OR_MAX_N + 1]; /* QP step                           */
+  double mu[OR_MAX_N];  /* QP multipliers of the dynamics                     */
+  double sigma[OR_MAX_N];                /* penalty weights after the update  */
+  double alpha[OR_TRACE_MAX_TRIALS];     /* step length of each trial         */
+  double f_trial[OR_TRACE_MAX_TRIALS];   /* objective at each trial point     */
+  double pen_trial[OR_TRACE_MAX_TRIALS]; /* sigma^T |g| at each trial point   */
+} or_sqp_trace_row;
+
+/* or_sqp with the trace: rows[0 .. *n_rows-1] (at most max_rows). */
+int or_sqp_traced(const or_model* m, const or_ctrl* c, double EaR, double x0,
+                  const double* zbar, double* u, double* x, double* lam, double* pil,
+                  double* piu, or_sqp_info* info, or_sqp_trace_row* rows, int max_rows,
+                  int* n_rows);
+
+/* The block-BFGS step of Sec. IV-C on all N + 1 packed blocks
+ * (W[3k .. 3k+2] = W11, W12, W22 of block k; block 0 = [u_0], blocks
+ * 1..N-1 = [x_k u_k], block N = [x_N]): each block is updated by the damped
+ * BFGS formula with s = (s_x[k], s_u[k]) and y = (y_x[k], y_u[k]), then, if any
+ * block is not positive definite, every block is reset to the identity.
+ * Returns 1 after a reset, else 0. */
+int or_bfgs_update_blocks(int N, double* W, const double* s_u, const double* s_x,
+                          const double* y_u, const double* y_x);
+
 /* ---- PI controller, Eq. (PI) ---- */
 double or_pi_step(const or_ctrl* c, double Ts, double ybar, double y, double ubar,
                   double* Ihat);

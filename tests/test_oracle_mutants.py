@@ -93,6 +93,32 @@ MUTANTS = [
      "Ihat = Ii + m->Ts * kaw * (uhat - u);",
      "Ihat = Ii + m->Ts * kaw * (u - uhat);",
      "test_oracle_grad.py", "real_part or richardson"),
+    ("SQP: penalty weights set to |mu| at every iteration", "or_sqp.c",
+     "sigma[k] = (l == 0) ? fabs(mu[k]) : fmax(fabs(mu[k]), 0.5 * (sigma[k] + fabs(mu[k])));",
+     "sigma[k] = fabs(mu[k]);",
+     "test_oracle_sqp_trace.py", "penalty"),
+    ("SQP: s_d averages the multipliers over N instead of 3N", "or_sqp.c",
+     "mult1 / (double)(3 * N)", "mult1 / (double)N",
+     "test_oracle_sqp_trace.py", "scaling"),
+    ("SQP: Armijo constant 0.1 instead of 1e-4", "or_sqp.c",
+     "c1 = 1e-4, beta_ls", "c1 = 0.1, beta_ls",
+     "test_oracle_sqp_trace.py", "armijo"),
+    ("SQP: step quartered instead of halved", "or_sqp.c",
+     "beta_ls = 0.5", "beta_ls = 0.25",
+     "test_oracle_sqp_trace.py", "armijo"),
+    ("SQP: Hessian reset disabled", "or_sqp.c",
+     "  if (!pd) {\n    for (int k = 0; k <= N; ++k) { Wb[k][0] = 1.0;",
+     "  if (0) {\n    for (int k = 0; k <= N; ++k) { Wb[k][0] = 1.0;",
+     "test_oracle_sqp_trace.py", "reset"),
+    ("SQP: reset of the offending block only", "or_sqp.c",
+     "    for (int k = 0; k <= N; ++k) { Wb[k][0] = 1.0; Wb[k][1] = 0.0; Wb[k][2] = 1.0; }\n    return 1;",
+     "    for (int k = 0; k <= N; ++k) if (!block_pd(k == 0 || k == N ? 1 : 2, Wb[k])) "
+     "{ Wb[k][0] = 1.0; Wb[k][1] = 0.0; Wb[k][2] = 1.0; }\n    return 1;",
+     "test_oracle_sqp_trace.py", "reset"),
+    ("SQP: convergence test ignores the state part of grad L", "or_sqp.c",
+     "for (int k = 1; k <= N; ++k) kg = fmax(kg, fabs(gx[k]));",
+     "for (int k = 1; k <= N; ++k) kg = fmax(kg, 0.0 * fabs(gx[k]));",
+     "test_oracle_sqp_trace.py", "scaling"),
 ]
 
 
