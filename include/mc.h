@@ -318,6 +318,19 @@ mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t pre
  * Tang's table-driven method; within about 1 ulp of the exact value. */
 mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host);
 
+/* Throughput probe of one arithmetic pipe on the current device, for the
+ * roofline of the simulation kernels (the paper has no counterpart: its
+ * timings are wall-clock on CPU cores).  kind: 0 FP64 fma chain, 1 fma + add,
+ * 2 the rate law's table-driven exp, 3 the library exp, 4 FP64 division,
+ * 5 log, 6 sqrt, 7 sincospi, 8 FP32 fma chain, 9 fma + expf, 10 FP32 fma +
+ * add.  One launch of 16 four-warp blocks per SM, every thread with 8
+ * independent chains of `iters` steps (1 .. 2^30).  *ms_out receives the
+ * launch's device time (CUDA events, after a short warm-up launch) and
+ * *steps_out the number of chain steps it ran, so steps / time is the
+ * probed operation's throughput.  Synchronises the device; allocates and
+ * frees one small device buffer.  MC_EINVAL for a bad kind or count. */
+mc_status mc_pipe_probe(int32_t kind, int64_t iters, double* ms_out, double* steps_out);
+
 /* Solve n structured QP subproblems, Eq. (QP-subproblem)/(nlpsqp_qp), with the
  * selected solver.  Inputs are n x N (A, B, b, r, lb, ub) and n x (N+1)
  * (Wxx, Wxu, Wuu, q) row-major host arrays (A[.,0], Wxx[.,0], Wxu[.,0],
@@ -377,7 +390,9 @@ mc_status mc_ocp_sens_batch(const mc_model_t* model, const mc_controller_t* ctrl
  * record, about 120 KB) is a file-scope __device__ array in the library: every
  * GPU that loads the library holds it until the process exits.  The first
  * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  All calls share
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process, so it assumes the device is not reset
+ * (cudaDeviceReset) while the library is loaded.  All calls share
  * the one array and each call overwrites what it reads, so calls that overlap
  * on the GPU (other streams, other host threads) race: serialise them.
  * The call enqueues two kernels on cuda_stream, waits for that stream and

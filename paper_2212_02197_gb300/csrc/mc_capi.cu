@@ -25,6 +25,7 @@
 #include "mc_qp_par.cuh"
 #include "mc_nmpc3.cuh"
 #include "mc_grad_nmpc.cuh"
+#include "mc_peaks.cuh"
 
 namespace mc {
 
@@ -598,6 +599,26 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   m->bV = mm->beta * mm->V;
   m->ib2 = 2.0 * m->ib;
   m->key0 = (uint32_t)seed; m->key1 = (uint32_t)(seed >> 32);
+  m->hEM = mm->Ts / (double)mm->n_em;
+  m->sqhEM = std::sqrt(m->hEM);
+  // first sample index of each set-point segment: the smallest i >= 0 with
+  // t0 + i Ts >= sp_time[s], the time formed as product then sum
+  m->sp_step[0] = 0;
+  for (int s = 1; s < mm->n_setpoints; ++s) {
+    const double est = (mm->sp_time[s] - mm->t0) / mm->Ts;
+    if (!(est < 2.0e9)) {
+      m->sp_step[s] = INT32_MAX;
+      continue;
+    }
+    int64_t i = est > 2.0 ? (int64_t)std::floor(est) - 2 : 0;
+    for (;;) {
+      volatile double prod = (double)i * mm->Ts;
+      const double t = mm->t0 + prod;
+      if (t >= mm->sp_time[s] || i >= INT32_MAX) break;
+      ++i;
+    }
+    m->sp_step[s] = (int)i;
+  }
   memset(c, 0, sizeof(*c));
   c->kind = cc->kind; c->precision = cc->precision; c->N = cc->N; c->n_rk4 = cc->n_rk4;
   c->sqp_max_it = cc->sqp_max_it; c->ls_max = cc->ls_max; c->qp_solver = cc->qp_solver;
@@ -1343,6 +1364,60 @@ mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host) {
   }
   cudaFree(dx);
   cudaFree(dy);
+  return s;
+}
+
+mc_status mc_pipe_probe(int32_t kind, int64_t iters, double* ms_out, double* steps_out) {
+  if (kind < 0 || kind >= kNumProbes || iters < 1 || iters > ((int64_t)1 << 30) || !ms_out ||
+      !steps_out)
+    return fail(nullptr, MC_EINVAL, "mc_pipe_probe: bad arguments");
+  int dev = 0, sms = 152;
+  MC_CUDA(nullptr, cudaGetDevice(&dev));
+  MC_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // 16 blocks of 4 warps per SM: enough warps per scheduler to keep any pipe busy
+  const unsigned blocks = (unsigned)sms * 16u;
+  const int64_t threads = (int64_t)blocks * 128;
+  double* out = nullptr;
+  if (cudaMalloc((void**)&out, sizeof(double) * threads) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, MC_ENOMEM, "mc_pipe_probe: allocation");
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  mc_status s = MC_OK;
+  auto launch = [&](int64_t it) {
+    switch (kind) {
+      case kProbeDfma: k_pipe_probe<kProbeDfma><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeNone: k_pipe_probe<kProbeNone><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeExpTab: k_pipe_probe<kProbeExpTab><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeExpLib: k_pipe_probe<kProbeExpLib><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeDiv: k_pipe_probe<kProbeDiv><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeLog: k_pipe_probe<kProbeLog><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeSqrt: k_pipe_probe<kProbeSqrt><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeSincos: k_pipe_probe<kProbeSincos><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeFfma: k_pipe_probe<kProbeFfma><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeExpf: k_pipe_probe<kProbeExpf><<<blocks, 128>>>(it, 1.0, out); break;
+      default: k_pipe_probe<kProbeNoneF><<<blocks, 128>>>(it, 1.0, out); break;
+    }
+  };
+  float ms = 0.f;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    s = fail(nullptr, MC_ECUDA, "mc_pipe_probe: cudaEventCreate failed");
+  } else {
+    launch(iters < 64 ? iters : 64);   // warm-up (clocks, instruction cache)
+    cudaEventRecord(a, 0);
+    launch(iters);
+    cudaEventRecord(b, 0);
+    const cudaError_t e = cudaEventSynchronize(b);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      s = cuda_fail(nullptr, e != cudaSuccess ? e : cudaErrorUnknown, "mc_pipe_probe");
+    else
+      cudaEventElapsedTime(&ms, a, b);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(out);
+  *ms_out = ms;
+  *steps_out = (double)threads * (double)kChains * (double)iters;
   return s;
 }
 

@@ -125,6 +125,8 @@ def lib():
             L.mc_ocp_sens_batch.restype = C.c_int
             L.mc_exp_batch.argtypes = [_dp, C.c_int64, _dp]
             L.mc_exp_batch.restype = C.c_int
+            L.mc_pipe_probe.argtypes = [C.c_int32, C.c_int64, _dp, _dp]
+            L.mc_pipe_probe.restype = C.c_int
             L.mc_set_pi_gains.argtypes = [H, C.c_double, C.c_double, C.c_double]
             L.mc_pi_grad.argtypes = [H, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]
             L.mc_grad_mean.argtypes = [H, _dp, C.c_int64]
@@ -214,6 +216,7 @@ class MonteCarlo:
         self._m, self._keep = make_model(model)
         self._c = make_ctrl(ctrl)
         self.n_sims = int(n_sims)
+        self.sqp_tol = float(ctrl["sqp_tol"]) if ctrl.get("kind") == "nmpc" else None
         self._h = C.c_void_p()
         _check(L.mc_create(C.byref(self._m), C.byref(self._c), self.n_sims, int(seed),
                            C.byref(self._h)))
@@ -356,6 +359,13 @@ def exp_batch(x):
     return y
 
 
+def pipe_probe(kind: int, iters: int):
+    """(device ms, chain steps) of one throughput-probe launch (mc_pipe_probe)."""
+    ms, steps = C.c_double(), C.c_double()
+    _check(lib().mc_pipe_probe(int(kind), int(iters), C.byref(ms), C.byref(steps)))
+    return ms.value, steps.value
+
+
 def philox(ctr, key):
     """Device Philox4x32-10 of counters ctr (n x 4 uint32) under key (2 words)."""
     ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
@@ -427,14 +437,45 @@ def _stats_dict(s: McStats, st: int) -> dict:
     return d
 
 
+def _check_device_array(t, name: str, dtype_name: str, n: int, cols: int | None):
+    """Reject anything the reduction's kernels could read past: the tensor must
+    be a contiguous CUDA tensor of the right dtype on the current device with
+    at least n rows (of `cols` columns)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a CUDA torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (got device {t.device})")
+    if t.dtype != getattr(torch, dtype_name):
+        raise ValueError(f"{name} must be {dtype_name} (got {t.dtype})")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, not on the current device "
+                         f"cuda:{torch.cuda.current_device()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if cols is None:
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} values, fewer than n = {n}")
+    elif t.dim() != 2 or t.shape[1] != cols or t.shape[0] < n:
+        raise ValueError(f"{name} must have shape (>= {n}, {cols}), not {tuple(t.shape)}")
+
+
 def reduce_noalloc(phi_dev, counters_dev, n: int, n_bins: int = 64, lo: float = 0.0,
                    hi: float = 0.0, stream=None) -> dict:
     """Statistics of per-trajectory results already on the device (CUDA torch
-    tensors: n float64 and n x N_COUNTERS int32), reduced without any device
-    allocation (see mc_reduce_noalloc in include/mc.h)."""
+    tensors on the current device: n float64 and n x N_COUNTERS int32),
+    reduced without any device allocation (see mc_reduce_noalloc in
+    include/mc.h).  Tensors of the wrong kind, device or size raise ValueError
+    before anything is launched."""
+    n = int(n)
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    _check_device_array(phi_dev, "phi_dev", "float64", n, None)
+    _check_device_array(counters_dev, "counters_dev", "int32", n, N_COUNTERS)
     s = McStats()
-    ptr = lambda t: C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
-    st = _check(lib().mc_reduce_noalloc(ptr(phi_dev), ptr(counters_dev), n, n_bins, lo, hi,
+    st = _check(lib().mc_reduce_noalloc(C.c_void_p(phi_dev.data_ptr()),
+                                        C.c_void_p(counters_dev.data_ptr()), n, n_bins, lo, hi,
                                         _stream_ptr(stream), C.byref(s)),
                 ok=(MC_OK, MC_WARN_NONFINITE))
     return _stats_dict(s, st)

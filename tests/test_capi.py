@@ -117,3 +117,20 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
             assert ctypes.sizeof(py) == int(value), cname
         else:
             assert getattr(py, field).offset == int(value), (cname, field)
+
+
+def test_reduce_noalloc_binding_rejects_bad_arrays_without_a_launch():
+    """The binding checks kind, dtype, layout and size of the device arrays
+    before it calls the library: nothing here reaches a GPU."""
+    import torch
+
+    from paper_2212_02197_gb300 import mc
+
+    phi = torch.zeros(8, dtype=torch.float64)
+    cnt = torch.zeros((8, mc.N_COUNTERS), dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA"):
+        mc.reduce_noalloc(phi, cnt, 8)
+    with pytest.raises(ValueError, match="CUDA torch tensor"):
+        mc.reduce_noalloc(123456, cnt, 8)
+    with pytest.raises(ValueError):
+        mc.reduce_noalloc(phi, cnt, -1)

@@ -41,14 +41,47 @@ def test_first_ocp_matches_oracle():
     assert np.mean(np.abs(cnt["sqp_iters"] - ref["sqp_iters"]) <= 1) >= 0.95
 
 
+@pytest.mark.parametrize("sched", ["persistent", "static"])
+def test_closed_loop_matches_oracle_tight(sched):
+    """The parity bar of the FP64 path, 1e-6 relative in Phi: 64 trajectories
+    x 60 steps with the T_in step and every OCP solved to 1e-8 on the scaled
+    KKT test (200 SQP iterations at most), where both implementations end at
+    the same KKT point up to the rounding floor of the merit function.
+
+    * Every trajectory whose OCPs all converged on both sides: within 1e-6.
+    * Every trajectory, with no exception: within 1e-5.  At this tolerance the
+      three-state SQP often stalls at the merit's rounding floor; where one
+      side's line search runs out of halvings and the other's runs on to the
+      iteration limit, the two stop at different iterates of the floor.
+      Trajectory 37 is the one case here: at its sample 25 the oracle's line
+      search fails after 543 SQP iterations in all, the GPU's runs to the
+      limit, and Phi moves by 1.26e-6.
+    * At least 95 % of all within 1e-6, the median within 1e-8."""
+    w = W.get(WL)
+    m = dict(w["model"], n_steps=60)
+    c = dict(w["nmpc"], sqp_tol=1e-8, sqp_max_it=200, schedule=sched)
+    n = 64
+    phi, cnt, st = _run(m, c, n, w["seed"])
+    ref = oracle.run(m, c, w["seed"], 0, n)
+    rel = np.abs(phi - ref["phi"]) / np.abs(ref["phi"])
+    stalled = ((ref["n_ocp_failed"] > 0) | (cnt["n_ocp_failed"] > 0) |
+               (ref["n_ls_fail"] > 0) | (cnt["n_ls_fail"] > 0))
+    assert np.all(rel[~stalled] <= 1e-6), (rel[~stalled].max(), int(np.argmax(np.where(stalled, 0, rel))))
+    assert np.all(rel <= 1e-5), (rel.max(), int(np.argmax(rel)))
+    assert np.mean(rel <= 1e-6) >= 0.95, np.sort(rel)[-5:]
+    assert np.median(rel) <= 1e-8
+    assert st["n_nonfinite"] == 0
+
+
 def test_closed_loop_matches_oracle():
-    """160 trajectories (5 warps), 60 steps, with the T_in step.  Each OCP
-    stops at the scaled KKT tolerance 1e-5 (Sec. IV, Eq. (convergence)); two
-    FP64 implementations that differ in rounding can stop at different
-    iterates inside it, after 9.5 SQP iterations per OCP on average.  So:
-    every trajectory whose OCPs all converged within 1e-5 relative in Phi,
-    95 % of them within 1e-6, and those with an OCP at the iteration limit
-    within 1e-3."""
+    """A secondary check at the workload's own tolerance: 160 trajectories
+    (5 warps), 60 steps, with the T_in step.  Each OCP stops at the scaled KKT
+    tolerance 1e-5 (Sec. IV, Eq. (convergence)); two FP64 implementations that
+    differ in rounding can stop at different iterates inside it, after 9.5 SQP
+    iterations per OCP on average.  So: every trajectory whose OCPs all
+    converged within 1e-5 relative in Phi, 95 % of them within 1e-6, and those
+    with an OCP at the iteration limit within 1e-3.  The 1e-6 bar itself is
+    held by the tight-tolerance test above."""
     w = W.get(WL)
     m = dict(w["model"], n_steps=60)
     n = 160

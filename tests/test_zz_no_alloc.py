@@ -60,9 +60,19 @@ def test_reduce_noalloc_matches_mc_stats_twice(kind):
 def test_reduce_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
 
+    import ctypes as C
+
     phi = torch.zeros(4, dtype=torch.float64, device="cuda")
     cnt = torch.zeros((4, mc.N_COUNTERS), dtype=torch.int32, device="cuda")
-    with pytest.raises(mc.McError, match="262144"):
-        mc.reduce_noalloc(phi, cnt, mc.MAX_NOALLOC_TRAJ + 1)
+    # the C entry point itself refuses n beyond its scratch, before any launch
+    s = mc.McStats()
+    st = mc.lib().mc_reduce_noalloc(C.c_void_p(phi.data_ptr()), C.c_void_p(cnt.data_ptr()),
+                                    mc.MAX_NOALLOC_TRAJ + 1, 64, 0.0, 0.0, C.c_void_p(0),
+                                    C.byref(s))
+    assert st == mc.MC_EINVAL
+    assert "262144" in mc.lib().mc_last_error(None).decode()
     with pytest.raises(mc.McError):
         mc.reduce_noalloc(phi, cnt, 4, n_bins=0)
+    # the binding refuses arrays shorter than n
+    with pytest.raises(ValueError):
+        mc.reduce_noalloc(phi, cnt, 5)
