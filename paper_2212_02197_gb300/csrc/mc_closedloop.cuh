@@ -33,14 +33,12 @@ __device__ __forceinline__ void plant_interval(const DevModel& m, const TrajPara
                                                uint32_t j, int i, double F, double n[3],
                                                const double* nzc = nullptr,
                                                int64_t nz_ld = 0) {
-  const double h = m.Ts / (double)m.n_em;
-  const R hR = (R)h, sqh = (R)sqrt(h);
+  const R hR = (R)m.hEM, sqh = (R)m.sqhEM;
   R nr[3] = {(R)n[0], (R)n[1], (R)n[2]};
   const R EaR = (R)tp.EaR, FR = (R)F;
   for (int s = 0; s < m.n_em; ++s) {
     const int64_t ks = (int64_t)i * m.n_em + s;
-    const double tau = m.t0 + (double)ks * h;
-    const double Tin = (m.dTin != 0.0 && tau >= tp.t_d) ? m.T_in + tp.dTin : m.T_in;
+    const double Tin = inlet_T_at(m, tp, ks);
     R xi[3];
     if (nzc) {
 #pragma unroll
@@ -64,14 +62,13 @@ __device__ TrajOut traj_pi(const DevModel& m, const DevCtrl& c, uint32_t j) {
   double phi = 0.0;
   R Ihat = 0;
   for (int i = 0; i <= K; ++i) {
-    const double t_i = m.t0 + (double)i * m.Ts;
     const double cT = n[2] / m.V;
     if (!isfinite(cT)) {
       out.cnt[6] = 1;
       phi = nan("");
       break;
     }
-    const double zi = zbar(m, t_i);
+    const double zi = zbar_at(m, i);
     const double ez = cT - zi;
     phi += ez * ez;
     if (i == K) break;
@@ -110,7 +107,7 @@ __device__ __forceinline__ void nmpc_begin(const DevModel& m, const DevCtrl& c, 
   T.F_prev = 0.0;
   T.phi = 0.0;
   T.out = TrajOut{};
-  double v0 = Fss(m, T.tp.EaR_c, zbar(m, m.t0)) / c.Fconv;
+  double v0 = Fss(m, T.tp.EaR_c, zbar_at(m, 0)) / c.Fconv;
   v0 = fmin(fmax(v0, c.vmin), c.vmax);
   const double ixs = 1.0 / c.x_scale;
   for (int k = 0; k < T.tp.N; ++k) {
@@ -130,14 +127,13 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
                                                  const Ws& w, NmpcTraj& T, SqpState& s,
                                                  bool shoot) {
   const int K = m.n_steps, N = T.tp.N;
-  const double t_i = m.t0 + (double)T.i * m.Ts;
   const double cT = T.n[2] / m.V;
   if (!isfinite(cT) || !isfinite(T.xhat) || !isfinite(T.P)) {
     T.out.cnt[6] = 1;
     T.out.phi = nan("");
     return false;
   }
-  const double ez = cT - zbar(m, t_i);
+  const double ez = cT - zbar_at(m, T.i);
   T.phi += ez * ez;
   if (T.i == K) {
     T.out.phi = T.phi / (double)(K + 1);
@@ -152,7 +148,7 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
   }
   ekf_filter(m, y, T.xhat, T.P);
   w(PIN, 0) = T.P;
-  for (int k = 1; k <= N; ++k) w(ZB, k) = zbar(m, m.t0 + (double)(T.i + k) * m.Ts);
+  for (int k = 1; k <= N; ++k) w(ZB, k) = zbar_at(m, T.i + k);
   if (c.Ru != 0.0)
     for (int k = 1; k <= N; ++k) w(VB, k) = Fss(m, T.tp.EaR_c, w(ZB, k)) / c.Fconv;
   sqp_start<R>(m, c, T.tp.EaR_c, T.xhat * (1.0 / c.x_scale), w, N, T.tp.max_it, T.i > 0, s,

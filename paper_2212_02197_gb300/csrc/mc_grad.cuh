@@ -52,9 +52,8 @@ __device__ __forceinline__ void em_step_adjoint(const DevModel& m, double EaR, d
 
 // Inlet temperature during substep ks (steps at t_d by dTin).
 __device__ __forceinline__ double inlet_T(const DevModel& m, const TrajParams& tp, int64_t ks,
-                                          double h) {
-  const double tau = m.t0 + (double)ks * h;
-  return (m.dTin != 0.0 && tau >= tp.t_d) ? m.T_in + tp.dTin : m.T_in;
+                                          double) {
+  return inlet_T_at(m, tp, ks);
 }
 
 // Trajectory j: Phi_j and dPhi_j / d(k_P, k_I, k_aw).  The checkpoints live in
@@ -76,13 +75,12 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
   double Ihat = 0.0, phi = 0.0, ezK = 0.0;
   bool finite = true;
   for (int i = 0; i <= K; ++i) {
-    const double t_i = m.t0 + (double)i * m.Ts;
     const double cT = n[2] / m.V;
     if (!isfinite(cT)) {
       finite = false;
       break;
     }
-    const double zi = zbar(m, t_i);
+    const double zi = zbar_at(m, i);
     const double ez = cT - zi;
     phi += ez * ez;
     if (i == K) {
@@ -112,7 +110,7 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
   phi_out[jj] = phi / (double)(K + 1);
 
   // ---- backward sweep
-  const double h = m.Ts / (double)m.n_em, sqh = sqrt(h);
+  const double h = m.hEM, sqh = m.sqhEM;
   const double umin = c.u_min / 60000.0, umax = c.u_max / 60000.0;
   const double Ts = m.Ts;
   double nb[3] = {0.0, 0.0, 2.0 * ezK * wK / m.V};
@@ -129,7 +127,7 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
       sn[i - i0][2] = nn[2];
       sn[i - i0][3] = Ih;
       const double cT = nn[2] / m.V;
-      const double zi = zbar(m, m.t0 + (double)i * m.Ts);
+      const double zi = zbar_at(m, i);
       const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
       const double F = pi_step<double>(c, m.Ts, zi, y, Fss(m, tp.EaR_c, zi), Ih);
       plant_interval<double>(m, tp, j, i, F, nn);
@@ -138,7 +136,7 @@ __global__ void __launch_bounds__(128) k_pi_grad(DevModel m, DevCtrl c, int64_t 
       double ns[3] = {sn[i - i0][0], sn[i - i0][1], sn[i - i0][2]};
       double Ih2 = sn[i - i0][3];
       const double cT = ns[2] / m.V;
-      const double zi = zbar(m, m.t0 + (double)i * m.Ts);
+      const double zi = zbar_at(m, i);
       const double y = cT + m.meas_sd * meas_noise<double>(m, j, (uint32_t)i);
       double e, uhat;
       const double F = pi_step<double>(c, m.Ts, zi, y, Fss(m, tp.EaR_c, zi), Ih2, &e, &uhat);

@@ -245,12 +245,11 @@ __device__ __forceinline__ void ekf_filter_tan(const DevModel& m, double y, doub
 __device__ void plant_interval_tan(const DevModel& m, const TrajParams& tp, uint32_t j, int i,
                                    double F, const double dF[3], const double n_in[3],
                                    double dn[3][3]) {
-  const double h = m.Ts / (double)m.n_em, sqh = sqrt(h);
+  const double h = m.hEM, sqh = m.sqhEM;
   double n[3] = {n_in[0], n_in[1], n_in[2]};
   for (int s = 0; s < m.n_em; ++s) {
     const int64_t ks = (int64_t)i * m.n_em + s;
-    const double tau = m.t0 + (double)ks * h;
-    const double Tin = (m.dTin != 0.0 && tau >= tp.t_d) ? m.T_in + tp.dTin : m.T_in;
+    const double Tin = inlet_T_at(m, tp, ks);
     double xi[3];
     process_noise<double>(m, j, (uint32_t)ks, xi);
     double f[3], J[9], fF[3];
@@ -287,13 +286,12 @@ __device__ TrajOut traj_nmpc_grad(const DevModel& m, const DevCtrl& c, uint32_t 
     // tangents of this sample's Phi term, measurement and CD-EKF, at the values
     // nmpc_sample starts from: the prediction the last OCP's interval-0
     // shooting carried, read before the next OCP's evaluation overwrites it
-    const double t_i = m.t0 + (double)T.i * m.Ts;
     const double cT = T.n[2] / m.V;
     const double xh0 = T.xhat, Ph0 = T.P, Fp = T.F_prev;
     const int i = T.i;
     const double xp = (i > 0) ? w(EPR, 0) : xh0, Pp = (i > 0) ? w(EPR, 1) : Ph0;
     if (isfinite(cT)) {
-      const double zi = zbar(m, t_i);
+      const double zi = zbar_at(m, i);
 #pragma unroll
       for (int d = 0; d < 3; ++d) dph[d] += 2.0 * (cT - zi) * dn[d][2] / m.V;
     }

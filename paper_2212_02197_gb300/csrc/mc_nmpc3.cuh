@@ -820,7 +820,7 @@ __device__ __forceinline__ void nmpc3_begin(const DevModel& m, const DevCtrl& c,
   T.F_prev = 0.0;
   T.phi = 0.0;
   T.out = TrajOut{};
-  double v0 = Fss(m, T.tp.EaR_c, zbar(m, m.t0)) / c.Fconv;
+  double v0 = Fss(m, T.tp.EaR_c, zbar_at(m, 0)) / c.Fconv;
   v0 = fmin(fmax(v0, c.vmin), c.vmax);
   for (int k = 0; k < N; ++k) {
     w(U3, k) = v0;
@@ -838,7 +838,6 @@ __device__ __forceinline__ void nmpc3_begin(const DevModel& m, const DevCtrl& c,
 __device__ __noinline__ bool nmpc3_sample(const DevModel& m, const DevCtrl& c, const Ws& w,
                                           Nmpc3Traj& T, Sqp3State& st) {
   const int N = T.tp.N, K = m.n_steps, i = T.i;
-  const double t_i = m.t0 + (double)i * m.Ts;
   const double cT = T.n[2] / m.V;
   bool bad = !isfinite(cT);
   for (int q = 0; q < 3; ++q) bad = bad || !isfinite(T.xh[q]);
@@ -848,7 +847,7 @@ __device__ __noinline__ bool nmpc3_sample(const DevModel& m, const DevCtrl& c, c
     T.out.phi = nan("");
     return false;
   }
-  const double ez = cT - zbar(m, t_i);
+  const double ez = cT - zbar_at(m, i);
   T.phi += ez * ez;
   if (i == K) {
     T.out.phi = T.phi / (double)(K + 1);
@@ -857,7 +856,7 @@ __device__ __noinline__ bool nmpc3_sample(const DevModel& m, const DevCtrl& c, c
   const double y = cT + m.meas_sd * meas_noise<double>(m, T.j, (uint32_t)i);
   if (i > 0) ekf3_predict(m, T.tp.EaR_c, c.n_rk4, T.F_prev, T.xh, T.P);
   ekf3_filter(m, y, T.xh, T.P);
-  for (int k = 1; k <= N; ++k) w(ZB3, k) = zbar(m, m.t0 + (double)(i + k) * m.Ts);
+  for (int k = 1; k <= N; ++k) w(ZB3, k) = zbar_at(m, i + k);
   for (int q = 0; q < 3; ++q) w(X3 + q, 0) = T.xh[q] / c.x_scale;
   sqp3_begin(w, N, T.tp.max_it, st);
   return true;
