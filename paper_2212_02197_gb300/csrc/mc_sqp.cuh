@@ -139,7 +139,9 @@ __device__ __forceinline__ void bfgs_block(int n, double& w11, double& w12, doub
   const double sr = (n == 1) ? s1 * r1 : s1 * r1 + s2 * r2;
   const double kappa = fmin(sWs, sr);
   if (!(kappa > eps_m)) return;
-  const double isWs = 1.0 / sWs, isr = 1.0 / sr;
+  // both reciprocals from one division (both factors exceed eps_m here)
+  const double inv = 1.0 / (sWs * sr);
+  const double isWs = sr * inv, isr = sWs * inv;
   w11 = w11 - Ws1 * Ws1 * isWs + r1 * r1 * isr;
   if (n == 2) {
     w12 = w12 - Ws1 * Ws2 * isWs + r1 * r2 * isr;
@@ -245,11 +247,12 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
     kg = fmax(kg, fmax(fabs(gu), fabs(gx)));
   }
   if (s.l > 0) {
-    // positive definiteness of every block, else reset all to the identity
+    // positive definiteness of every block (Cholesky pivots a and d - b^2/a,
+    // the second tested as a d - b^2 > 0 for a > 0), else reset all to the identity
     bool pd = w(WUU, 0) > 0.0 && w(WXX, N) > 0.0;
     for (int k = 1; k < N; ++k) {
       const double a = w(WXX, k), b = w(WXU, k), d = w(WUU, k);
-      pd = pd && (a > 0.0) && (d - b * b / a > 0.0);
+      pd = pd && (a > 0.0) && (a * d - b * b > 0.0);
     }
     if (!pd) {
       for (int k = 0; k <= N; ++k) {
