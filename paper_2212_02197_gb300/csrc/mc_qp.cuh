@@ -107,11 +107,142 @@ MC_HD bool riccati_backward(const Ws& w, int N, uint64_t fixed, RkF rk_of,
 // ---------------------------------------------------------------------------
 // Primal active-set method.  Reads EA, EB, EG (= b), WXX, WXU, WUU, EQ (= q),
 // QR (= r, if has_r), LB, UB; writes DU, DX, MU, NUL, NUU.
+//
+// The arrays are handed to the solver as separate columns (element k of a
+// column at c[k * ld]) through restrict-qualified pointers: they are disjoint
+// rows of the scratch, and saying so lets the compiler issue the loads of the
+// next stages while the stores of the current one are pending.  The recursions
+// are latency-bound per lane, so this overlap, not the arithmetic, sets their
+// speed.  Same operations as the plain formulation, stage by stage.
+MC_HD double* ws_col(const Ws& w, int a) { return w.p + (int64_t)a * w.N1 * w.ld; }
+
+// Backward Riccati sweep of the active-set method (input weight Wuu, inputs in
+// `fixed` held at du): stores P_{k+1}, p_{k+1}, K_k, k_k; false on a pivot <= 0.
+MC_HD bool as_backward(int N, int64_t ld, uint64_t fixed, bool has_r,
+                       const double* __restrict__ A_, const double* __restrict__ B_,
+                       const double* __restrict__ b_, const double* __restrict__ q_,
+                       const double* __restrict__ r_, const double* __restrict__ Wxx,
+                       const double* __restrict__ Wxu, const double* __restrict__ Wuu,
+                       const double* __restrict__ du_, double* __restrict__ P_,
+                       double* __restrict__ p_, double* __restrict__ K_,
+                       double* __restrict__ kf_) {
+  double P = Wxx[N * ld], p = q_[N * ld];
+#pragma unroll 2
+  for (int k = N - 1; k >= 0; --k) {
+    const int64_t o = k * ld;
+    const double A = (k > 0) ? A_[o] : 0.0;
+    const double B = B_[o];
+    const double b = b_[o];
+    const double Pbp = P * b + p;
+    P_[o + ld] = P;
+    p_[o + ld] = p;
+    double Pn = 0.0, pn = 0.0;
+    if ((fixed >> k) & 1ull) {
+      const double c = du_[o];
+      K_[o] = 0.0;
+      kf_[o] = c;
+      if (k > 0) {
+        Pn = Wxx[o] + A * A * P;
+        pn = q_[o] + Wxu[o] * c + A * (P * (B * c) + Pbp);
+      }
+    } else {
+      const double Rb = Wuu[o] + B * B * P;
+      if (!(Rb > 0.0)) return false;
+      const double iR = 1.0 / Rb;
+      const double Sb = (k > 0) ? Wxu[o] + A * P * B : 0.0;
+      const double sb = (has_r ? r_[o] : 0.0) + B * Pbp;
+      K_[o] = -Sb * iR;
+      kf_[o] = -sb * iR;
+      if (k > 0) {
+        Pn = Wxx[o] + A * A * P - Sb * Sb * iR;
+        pn = q_[o] + A * Pbp - Sb * sb * iR;
+      }
+    }
+    P = Pn;
+    p = pn;
+  }
+  return true;
+}
+
+// Forward sweep (subspace minimiser z, states, dynamics multipliers) fused with
+// the ratio test over the free inputs: returns the blocking stage (-1 if none),
+// its side and the step length alpha.
+MC_HD int as_forward(int N, int64_t ld, uint64_t fixed, const double* __restrict__ A_,
+                     const double* __restrict__ B_, const double* __restrict__ b_,
+                     const double* __restrict__ P_, const double* __restrict__ p_,
+                     const double* __restrict__ K_, const double* __restrict__ kf_,
+                     const double* __restrict__ lb_, const double* __restrict__ ub_,
+                     const double* __restrict__ du_, double* __restrict__ z_,
+                     double* __restrict__ dx_, double* __restrict__ mu_, double& alpha,
+                     bool& block_lo) {
+  double dx = 0.0;
+  alpha = 1.0;
+  int block = -1;
+  block_lo = false;
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    const double A = (k > 0) ? A_[o] : 0.0;
+    const double z = K_[o] * dx + kf_[o];
+    const double dxn = A * dx + B_[o] * z + b_[o];
+    z_[o] = z;
+    dx_[o + ld] = dxn;
+    mu_[o] = -(P_[o + ld] * dxn + p_[o + ld]);
+    dx = dxn;
+    if ((fixed >> k) & 1ull) continue;
+    const double du = du_[o];
+    const double lb = lb_[o], ub = ub_[o];
+    const double pk = z - du;
+    if (pk < 0.0 && z < lb) {
+      const double t = (lb - du) / pk;
+      if (t < alpha) { alpha = t; block = k; block_lo = true; }
+    } else if (pk > 0.0 && z > ub) {
+      const double t = (ub - du) / pk;
+      if (t < alpha) { alpha = t; block = k; block_lo = false; }
+    }
+  }
+  return block;
+}
+
+// At a subspace minimiser: du = z on the free stages, and the working-set
+// multipliers; returns the stage with the most negative one (-1: optimal).
+MC_HD int as_multipliers(int N, int64_t ld, uint64_t fixed, uint64_t lo, bool has_r,
+                         double mult_tol, const double* __restrict__ B_,
+                         const double* __restrict__ r_, const double* __restrict__ Wxu,
+                         const double* __restrict__ Wuu, const double* __restrict__ z_,
+                         const double* __restrict__ dx_, const double* __restrict__ mu_,
+                         double* __restrict__ du_) {
+  int worst = -1;
+  double worst_val = -mult_tol;
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    const bool f = (fixed >> k) & 1ull;
+    const double du = f ? du_[o] : z_[o];
+    du_[o] = du;
+    if (!f) continue;
+    const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
+    const double v = Wuu[o] * du + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
+    const double lam = ((lo >> k) & 1ull) ? v : -v;
+    if (lam < worst_val) { worst_val = lam; worst = k; }
+  }
+  return worst;
+}
+
 MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
+  const int64_t ld = w.ld;
+  const double *A_ = ws_col(w, EA), *B_ = ws_col(w, EB), *b_ = ws_col(w, EG),
+               *q_ = ws_col(w, EQ), *r_ = ws_col(w, QR), *Wxx = ws_col(w, WXX),
+               *Wxu = ws_col(w, WXU), *Wuu = ws_col(w, WUU), *lb_ = ws_col(w, LB),
+               *ub_ = ws_col(w, UB);
+  double *du_ = ws_col(w, DU), *dx_ = ws_col(w, DX), *mu_ = ws_col(w, MU),
+         *nul_ = ws_col(w, NUL), *nuu_ = ws_col(w, NUU), *P_ = ws_col(w, RP),
+         *p_ = ws_col(w, RPP), *K_ = ws_col(w, RK), *kf_ = ws_col(w, RKF), *z_ = ws_col(w, RZ);
   uint64_t lo = 0, up = 0;
   double gscale = 1.0;
   for (int k = 0; k < N; ++k) {
-    const double lb = w(LB, k), ub = w(UB, k);
+    const int64_t o = k * ld;
+    const double lb = lb_[o], ub = ub_[o];
     double du = 0.0;
     if (lb >= 0.0) {
       lo |= 1ull << k;
@@ -120,81 +251,44 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
       up |= 1ull << k;
       du = ub;
     }
-    w(DU, k) = du;
-    gscale = fmax(gscale, fabs(w(EQ, k + 1)));
-    if (has_r) gscale = fmax(gscale, fabs(w(QR, k)));
+    du_[o] = du;
+    gscale = fmax(gscale, fabs(q_[o + ld]));
+    if (has_r) gscale = fmax(gscale, fabs(r_[o]));
   }
   const double mult_tol = 1e-13 * gscale;
-  auto rk_of = [&](int k) { return has_r ? w(QR, k) : 0.0; };
-  auto bk_of = [&](int k) { return w(EG, k); };
-  auto qk_of = [&](int k) { return w(EQ, k); };
-  auto zero = [&](int) { return 0.0; };
 
   QpResult res{0, 1};
   for (int it = 0; it < max_it; ++it) {
     res.iters = it + 1;
     const uint64_t fixed = lo | up;
-    if (!riccati_backward(w, N, fixed, rk_of, bk_of, qk_of, zero, false)) {
+    if (!as_backward(N, ld, fixed, has_r, A_, B_, b_, q_, r_, Wxx, Wxu, Wuu, du_, P_, p_, K_,
+                     kf_)) {
       res.status = 2;
       return res;
     }
-    // forward sweep: subspace minimiser z, its states and multipliers
-    double dx = 0.0;
-    for (int k = 0; k < N; ++k) {
-      const double A = (k > 0) ? w(EA, k) : 0.0;
-      const double z = w(RK, k) * dx + w(RKF, k);
-      const double dxn = A * dx + w(EB, k) * z + w(EG, k);
-      w(RZ, k) = z;
-      w(DX, k + 1) = dxn;
-      w(MU, k) = -(w(RP, k + 1) * dxn + w(RPP, k + 1));
-      dx = dxn;
-    }
-    // ratio test over the free inputs
-    double alpha = 1.0;
-    int block = -1;
-    bool block_lo = false;
-    for (int k = 0; k < N; ++k) {
-      if ((fixed >> k) & 1ull) continue;
-      const double z = w(RZ, k), du = w(DU, k);
-      const double lb = w(LB, k), ub = w(UB, k);
-      const double pk = z - du;
-      if (pk < 0.0 && z < lb) {
-        const double t = (lb - du) / pk;
-        if (t < alpha) { alpha = t; block = k; block_lo = true; }
-      } else if (pk > 0.0 && z > ub) {
-        const double t = (ub - du) / pk;
-        if (t < alpha) { alpha = t; block = k; block_lo = false; }
-      }
-    }
+    double alpha;
+    bool block_lo;
+    const int block = as_forward(N, ld, fixed, A_, B_, b_, P_, p_, K_, kf_, lb_, ub_, du_, z_,
+                                 dx_, mu_, alpha, block_lo);
     if (block >= 0) {
       if (alpha < 0.0) alpha = 0.0;
       for (int k = 0; k < N; ++k) {
         if ((fixed >> k) & 1ull) continue;
-        const double du = w(DU, k);
-        w(DU, k) = du + alpha * (w(RZ, k) - du);
+        const int64_t o = k * ld;
+        const double du = du_[o];
+        du_[o] = du + alpha * (z_[o] - du);
       }
       if (block_lo) {
         lo |= 1ull << block;
-        w(DU, block) = w(LB, block);
+        du_[block * ld] = lb_[block * ld];
       } else {
         up |= 1ull << block;
-        w(DU, block) = w(UB, block);
+        du_[block * ld] = ub_[block * ld];
       }
       continue;
     }
-    // subspace minimiser reached; multipliers of the working set
-    int worst = -1;
-    double worst_val = -mult_tol;
-    for (int k = 0; k < N; ++k) {
-      const bool f = (fixed >> k) & 1ull;
-      const double du = f ? w(DU, k) : w(RZ, k);
-      w(DU, k) = du;
-      if (!f) continue;
-      const double cross = (k > 0) ? w(WXU, k) * w(DX, k) : 0.0;
-      const double v = w(WUU, k) * du + cross + rk_of(k) - w(MU, k) * w(EB, k);
-      const double lam = ((lo >> k) & 1ull) ? v : -v;
-      if (lam < worst_val) { worst_val = lam; worst = k; }
-    }
+    const int worst = as_multipliers(N, ld, fixed, lo, has_r, mult_tol, B_, r_, Wxu, Wuu, z_,
+                                     dx_, mu_, du_);
     if (worst < 0) {
       res.status = 0;
       break;
@@ -204,16 +298,17 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
   }
   // bound multipliers from stationarity in du
   for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
     double nl = 0.0, nu = 0.0;
     if (((lo | up) >> k) & 1ull) {
-      const double cross = (k > 0) ? w(WXU, k) * w(DX, k) : 0.0;
-      const double v = w(WUU, k) * w(DU, k) + cross + rk_of(k) - w(MU, k) * w(EB, k);
+      const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
+      const double v = Wuu[o] * du_[o] + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
       if ((lo >> k) & 1ull) nl = v; else nu = -v;
     }
-    w(NUL, k) = nl;
-    w(NUU, k) = nu;
+    nul_[o] = nl;
+    nuu_[o] = nu;
   }
-  w(DX, 0) = 0.0;
+  dx_[0] = 0.0;
   return res;
 }
 

@@ -57,6 +57,24 @@ __device__ __noinline__ void shoot_interval(const DevModel& m, const DevCtrl& c,
   Ppr = (double)P1;
 }
 
+// The objective's stage terms Q_z (z_k - zbar_k)^2 T_s, k = 1..N, and their
+// gradients q_k at the states x (columns as in the SQP passes).
+__device__ __forceinline__ double objective_pass(int N, int64_t ld, double Qz, double Ts,
+                                                 double xs, double iV, double qf,
+                                                 const double* __restrict__ x_,
+                                                 const double* __restrict__ zb_,
+                                                 double* __restrict__ q_) {
+  double f = 0.0;
+#pragma unroll 2
+  for (int k = 1; k <= N; ++k) {
+    const int64_t o = k * ld;
+    const double dz = x_[o] * xs * iV - zb_[o];
+    f += Qz * dz * dz * Ts;
+    q_[o] = qf * dz;
+  }
+  return f;
+}
+
 // Which intervals evaluate integrates.
 enum RkMode : int {
   kRkAll = 0,   // every interval
@@ -65,6 +83,27 @@ enum RkMode : int {
                 // the same (x_k, u_k)
   kRkNone = 2   // none: the arrays were filled by the shooting pool
 };
+
+// The extended objective's terms, R_u (v_k - vbar_{k+1})^2 T_s and
+// Q_n (z_N - zbar_N)^2 (zero in the paper's objective), and Q_n's gradient.
+__device__ __forceinline__ double objective_extra(const DevModel& m, const DevCtrl& c, int N,
+                                                  const Ws& w, int u_arr, int x_arr,
+                                                  int q_arr) {
+  double f = 0.0;
+  const double xs = c.x_scale;
+  if (c.Ru != 0.0) {
+    for (int k = 0; k < N; ++k) {
+      const double dv = w(u_arr, k) - w(VB, k + 1);
+      f += c.Ru * dv * dv * m.Ts;
+    }
+  }
+  if (c.Qn != 0.0) {
+    const double dz = w(x_arr, N) * xs * m.iV - w(ZB, N);
+    f += c.Qn * dz * dz;
+    w(q_arr, N) += 2.0 * c.Qn * dz * xs * m.iV;
+  }
+  return f;
+}
 
 // Shooting of the intervals selected by rk_mode at the point (u_arr, x_arr),
 // writing A_k, B_k, g_k into (a_arr, b_arr, g_arr) and q_k = df/dx_k into
@@ -81,6 +120,10 @@ __device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, dou
                                            int rk_mode) {
   const double xs = c.x_scale, ixs = 1.0 / c.x_scale;
   const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
+  if (rk_mode == kRkNone)  // the pool shot the intervals: the objective pass only
+    return objective_pass(N, w.ld, c.Qz, m.Ts, xs, m.iV, qf, ws_col(w, x_arr), ws_col(w, ZB),
+                          ws_col(w, q_arr)) +
+           objective_extra(m, c, N, w, u_arr, x_arr, q_arr);
   double f = 0.0;
   double xk = w(X, 0);
   const int pr_arr = (a_arr == TA) ? TPR : EPR;
@@ -103,19 +146,7 @@ __device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, dou
     w(q_arr, k + 1) = qf * dz;
     xk = xn;
   }
-  // extended objective: R_u (v_k - vbar_{k+1})^2 T_s and Q_n (z_N - zbar_N)^2
-  if (c.Ru != 0.0) {
-    for (int k = 0; k < N; ++k) {
-      const double dv = w(u_arr, k) - w(VB, k + 1);
-      f += c.Ru * dv * dv * m.Ts;
-    }
-  }
-  if (c.Qn != 0.0) {
-    const double dz = w(x_arr, N) * xs * m.iV - w(ZB, N);
-    f += c.Qn * dz * dz;
-    w(q_arr, N) += 2.0 * c.Qn * dz * xs * m.iV;
-  }
-  return f;
+  return f + objective_extra(m, c, N, w, u_arr, x_arr, q_arr);
 }
 
 // Damped BFGS update of one packed block (Sec. IV-C); n = 1 or 2.
@@ -150,12 +181,30 @@ __device__ __forceinline__ void bfgs_block(int n, double& w11, double& w12, doub
 }
 
 // Trial point xi + alpha dxi (u clipped into its bounds against rounding).
+// The per-lane passes below take the scratch rows as separate columns through
+// restrict-qualified pointers (element k at c[k * ld]; the rows are disjoint),
+// so that the compiler may issue the next stages' loads while the current
+// stage's stores are pending: these passes are bound by memory latency, not by
+// their arithmetic.
+__device__ __forceinline__ void trial_point_pass(int N, int64_t ld, double alpha, double vmin,
+                                                 double vmax, const double* __restrict__ u_,
+                                                 const double* __restrict__ du_,
+                                                 const double* __restrict__ x_,
+                                                 const double* __restrict__ dx_,
+                                                 double* __restrict__ ut_,
+                                                 double* __restrict__ xt_) {
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    ut_[o] = fmin(fmax(u_[o] + alpha * du_[o], vmin), vmax);
+    xt_[o + ld] = x_[o + ld] + alpha * dx_[o + ld];
+  }
+}
+
 __device__ __forceinline__ void sqp_trial_point(const DevCtrl& c, const Ws& w,
                                                 const SqpState& s) {
-  for (int k = 0; k < s.N; ++k) {
-    w(UT, k) = fmin(fmax(w(U, k) + s.alpha * w(DU, k), c.vmin), c.vmax);
-    w(XT, k + 1) = w(X, k + 1) + s.alpha * w(DX, k + 1);
-  }
+  trial_point_pass(s.N, w.ld, s.alpha, c.vmin, c.vmax, ws_col(w, U), ws_col(w, DU),
+                   ws_col(w, X), ws_col(w, DX), ws_col(w, UT), ws_col(w, XT));
 }
 
 // Start an OCP from the warm start in (U, X, LAM, PIL, PIU) with x0 and the
@@ -198,74 +247,136 @@ __device__ __forceinline__ void sqp_start_eval(const DevModel& m, const DevCtrl&
 // true when the OCP is finished (s.info.status set).  Otherwise solves the QP,
 // updates the l1 penalty weights, forms T(0) and its slope and prepares the
 // first trial point (alpha = 1).
+// First pass of an SQP iteration: Lagrangian gradient at the current point
+// (its infinity norm kg and the multipliers' 1-norm), for l > 0 the damped
+// block BFGS of every block with the positive-definiteness test of the
+// updated blocks, max |g_k| and the QP bounds.  GLX(k) holds, on entry, the
+// new-point x-gradient of stage k minus its old-point value (written by the
+// previous stage of this pass), the s-y pair's x part of block k.
+__device__ __forceinline__ void check_pass(
+    int N, int64_t ld, bool bfgs, double alpha, bool has_r, double vmin, double vmax,
+    const double* __restrict__ lam_, const double* __restrict__ pil_,
+    const double* __restrict__ piu_, const double* __restrict__ A_,
+    const double* __restrict__ B_, const double* __restrict__ g_, const double* __restrict__ q_,
+    const double* __restrict__ r_, const double* __restrict__ du_,
+    const double* __restrict__ dx_, const double* __restrict__ glu_,
+    double* __restrict__ glx_, double* __restrict__ wxx_, double* __restrict__ wxu_,
+    double* __restrict__ wuu_, const double* __restrict__ u_, double* __restrict__ lb_,
+    double* __restrict__ ub_, double& kg, double& ke, double& mult1, bool& pd) {
+  kg = 0.0;
+  ke = 0.0;
+  mult1 = 0.0;
+  pd = true;
+  double lam = lam_[0];
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    const double pil = pil_[o], piu = piu_[o];
+    mult1 += fabs(lam) + fabs(pil) + fabs(piu);
+    double gu = -lam * B_[o] - pil + piu;
+    if (has_r) gu += r_[o];
+    double gx, lam_n = 0.0;
+    if (k + 1 < N) {
+      lam_n = lam_[o + ld];
+      gx = q_[o + ld] - lam_n * A_[o + ld] + lam;
+    } else {
+      gx = q_[o + ld] + lam;
+    }
+    if (bfgs) {
+      // damped block BFGS with s = alpha (du, dx) and
+      // y = grad L(xi^[l], .) - grad L(xi^[l-1], .) at the new multipliers
+      const double su = alpha * du_[o], sx = alpha * dx_[o];
+      const double yu = gu - glu_[o], yx = (k > 0) ? glx_[o] : 0.0;
+      if (k == 0) {
+        double w11 = wuu_[0], w12 = 0.0, w22 = 0.0;
+        bfgs_block(1, w11, w12, w22, su, 0.0, yu, 0.0);
+        wuu_[0] = w11;
+        pd = pd && (w11 > 0.0);
+      } else {
+        double w11 = wxx_[o], w12 = wxu_[o], w22 = wuu_[o];
+        bfgs_block(2, w11, w12, w22, sx, su, yx, yu);
+        wxx_[o] = w11;
+        wxu_[o] = w12;
+        wuu_[o] = w22;
+        // Cholesky pivots a and d - b^2/a, the second tested as a d - b^2 > 0
+        pd = pd && (w11 > 0.0) && (w11 * w22 - w12 * w12 > 0.0);
+      }
+      const double glx_n = glx_[o + ld];
+      if (k == N - 1) {
+        double wn = wxx_[o + ld], d0 = 0.0, d1 = 0.0;
+        bfgs_block(1, wn, d0, d1, alpha * dx_[o + ld], 0.0, gx - glx_n, 0.0);
+        wxx_[o + ld] = wn;
+        pd = pd && (wn > 0.0);
+      }
+      // keep the new-point x-gradient of stage k+1 for its block
+      glx_[o + ld] = gx - glx_n;
+    }
+    kg = fmax(kg, fmax(fabs(gu), fabs(gx)));
+    ke = fmax(ke, fabs(g_[o]));
+    const double u = u_[o];
+    lb_[o] = vmin - u;
+    ub_[o] = vmax - u;
+    lam = lam_n;
+  }
+}
+
+// The sigma update of the l1 penalty weights (Sec. IV-B), the penalty and the
+// merit slope's objective part, fused with the first trial point (alpha = 1).
+__device__ __forceinline__ void penalty_pass(
+    int N, int64_t ld, bool first, bool has_r, double vmin, double vmax,
+    const double* __restrict__ mu_, double* __restrict__ sig_, const double* __restrict__ g_,
+    const double* __restrict__ q_, const double* __restrict__ r_,
+    const double* __restrict__ du_, const double* __restrict__ dx_,
+    const double* __restrict__ u_, const double* __restrict__ x_, double* __restrict__ ut_,
+    double* __restrict__ xt_, double& pen, double& dfd) {
+  pen = 0.0;
+  dfd = 0.0;
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    const double am = fabs(mu_[o]);
+    const double sg = first ? am : fmax(am, 0.5 * (sig_[o] + am));
+    sig_[o] = sg;
+    pen += sg * fabs(g_[o]);
+    const double dxn = dx_[o + ld];
+    dfd += q_[o + ld] * dxn;
+    const double du = du_[o];
+    if (has_r) dfd += r_[o] * du;
+    ut_[o] = fmin(fmax(u_[o] + 1.0 * du, vmin), vmax);
+    xt_[o + ld] = x_[o + ld] + 1.0 * dxn;
+  }
+}
+
+// Top of an SQP iteration at xi^[l] (evaluated): damped block BFGS for l > 0,
+// the scaled KKT test of Eq. (convergence) and the iteration limit.  Returns
+// true when the OCP is finished (s.info.status set).  Otherwise solves the QP,
+// updates the l1 penalty weights, forms T(0) and its slope and prepares the
+// first trial point (alpha = 1).
 __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, SqpState& s) {
   const int N = s.N;
+  const int64_t ld = w.ld;
   const double s_max = 100.0;
-  double kg = 0.0, ke = 0.0, mult1 = 0.0;
   const bool has_r = (c.Ru != 0.0);
   if (has_r)  // input gradient r_k = 2 R_u (v_k - vbar_{k+1}) T_s at the current point
     for (int k = 0; k < N; ++k) w(QR, k) = c.r_scale * (w(U, k) - w(VB, k + 1));
-  for (int k = 0; k < N; ++k) {
-    const double lam = w(LAM, k), pil = w(PIL, k), piu = w(PIU, k);
-    mult1 += fabs(lam) + fabs(pil) + fabs(piu);
-    double gu = -lam * w(EB, k) - pil + piu;
-    if (has_r) gu += w(QR, k);
-    double gx;
-    if (k + 1 < N)
-      gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
-    else
-      gx = w(EQ, N) + lam;
-    if (s.l > 0) {
-      // damped block BFGS with s = alpha (du, dx) and
-      // y = grad L(xi^[l], .) - grad L(xi^[l-1], .) at the new multipliers
-      const double su = s.alpha * w(DU, k), sx = s.alpha * w(DX, k);
-      const double yu = gu - w(GLU, k), yx = (k > 0) ? w(GLX, k) : 0.0;
-      double w11, w12, w22;
-      if (k == 0) {
-        w11 = w(WUU, 0);
-        w12 = 0.0;
-        w22 = 0.0;
-        bfgs_block(1, w11, w12, w22, su, 0.0, yu, 0.0);
-        w(WUU, 0) = w11;
-      } else {
-        w11 = w(WXX, k);
-        w12 = w(WXU, k);
-        w22 = w(WUU, k);
-        bfgs_block(2, w11, w12, w22, sx, su, yx, yu);
-        w(WXX, k) = w11;
-        w(WXU, k) = w12;
-        w(WUU, k) = w22;
-      }
-      if (k == N - 1) {
-        double wn = w(WXX, N), d0 = 0.0, d1 = 0.0;
-        bfgs_block(1, wn, d0, d1, s.alpha * w(DX, N), 0.0, gx - w(GLX, N), 0.0);
-        w(WXX, N) = wn;
-      }
-      // keep the new-point x-gradient of stage k+1 for its block
-      w(GLX, k + 1) = gx - w(GLX, k + 1);
+  double kg, ke, mult1;
+  bool pd;
+  check_pass(N, ld, s.l > 0, s.alpha, has_r, c.vmin, c.vmax, ws_col(w, LAM), ws_col(w, PIL),
+             ws_col(w, PIU), ws_col(w, EA), ws_col(w, EB), ws_col(w, EG), ws_col(w, EQ),
+             ws_col(w, QR), ws_col(w, DU), ws_col(w, DX), ws_col(w, GLU), ws_col(w, GLX),
+             ws_col(w, WXX), ws_col(w, WXU), ws_col(w, WUU), ws_col(w, U), ws_col(w, LB),
+             ws_col(w, UB), kg, ke, mult1, pd);
+  if (s.l > 0 && !pd) {
+    // a block is not positive definite: reset all of them to the identity
+    for (int k = 0; k <= N; ++k) {
+      w(WXX, k) = 1.0;
+      w(WXU, k) = 0.0;
+      w(WUU, k) = 1.0;
     }
-    kg = fmax(kg, fmax(fabs(gu), fabs(gx)));
-  }
-  if (s.l > 0) {
-    // positive definiteness of every block (Cholesky pivots a and d - b^2/a,
-    // the second tested as a d - b^2 > 0 for a > 0), else reset all to the identity
-    bool pd = w(WUU, 0) > 0.0 && w(WXX, N) > 0.0;
-    for (int k = 1; k < N; ++k) {
-      const double a = w(WXX, k), b = w(WXU, k), d = w(WUU, k);
-      pd = pd && (a > 0.0) && (a * d - b * b > 0.0);
-    }
-    if (!pd) {
-      for (int k = 0; k <= N; ++k) {
-        w(WXX, k) = 1.0;
-        w(WXU, k) = 0.0;
-        w(WUU, k) = 1.0;
-      }
-      s.info.n_hess_reset++;
-    }
+    s.info.n_hess_reset++;
   }
   const double s_d = fmax(s_max, mult1 / (3.0 * N)) / s_max;
   kg /= s_d;
-  for (int k = 0; k < N; ++k) ke = fmax(ke, fabs(w(EG, k)));
   s.info.kkt_grad = kg;
   s.info.kkt_eq = ke;
   s.info.f = s.f;
@@ -278,33 +389,22 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
     return true;
   }
 
-  // QP subproblem at xi^[l]
-  for (int k = 0; k < N; ++k) {
-    const double u = w(U, k);
-    w(LB, k) = c.vmin - u;
-    w(UB, k) = c.vmax - u;
-  }
+  // QP subproblem at xi^[l] (bounds LB, UB from the first pass)
   const QpResult qr = (c.qp_solver == 1) ? qp_ipm(w, N, has_r, c.ip_max_it, c.ip_tol)
                                          : qp_active_set(w, N, has_r, 10 * N + 20);
   s.info.qp_iters += qr.iters;
   if (qr.status != 0) s.info.qp_fail++;
   s.info.iters++;
 
-  // penalty weights (sigma update) and the merit slope
-  double pen = 0.0, dfd = 0.0;
-  for (int k = 0; k < N; ++k) {
-    const double am = fabs(w(MU, k));
-    const double sg = (s.l == 0) ? am : fmax(am, 0.5 * (w(SIG, k) + am));
-    w(SIG, k) = sg;
-    pen += sg * fabs(w(EG, k));
-    dfd += w(EQ, k + 1) * w(DX, k + 1);
-    if (has_r) dfd += w(QR, k) * w(DU, k);
-  }
+  // penalty weights (sigma update), the merit slope and the first trial point
+  double pen, dfd;
+  penalty_pass(N, ld, s.l == 0, has_r, c.vmin, c.vmax, ws_col(w, MU), ws_col(w, SIG),
+               ws_col(w, EG), ws_col(w, EQ), ws_col(w, QR), ws_col(w, DU), ws_col(w, DX),
+               ws_col(w, U), ws_col(w, X), ws_col(w, UT), ws_col(w, XT), pen, dfd);
   s.T0 = s.f + pen;
   s.DT0 = dfd - pen;
   s.alpha = 1.0;
   s.hv = 0;
-  sqp_trial_point(c, w, s);
   return false;
 }
 
@@ -322,6 +422,56 @@ __device__ __forceinline__ void sqp_eval_trial_shot(const DevModel& m, const Dev
                                                     double EaR, const Ws& w, SqpState& s) {
   s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ, kRkNone);
   s.info.ls_trials++;
+}
+
+// An accepted step, one pass over the stages: the multipliers step by alpha
+// towards the QP's, the old-point Lagrangian gradient at the new multipliers
+// (GLU, GLX; r at the old point) is kept for BFGS, and the trial point and its
+// evaluation become current; the step actually taken (after the bound clip)
+// is what BFGS sees.  lam of stage k+1 is stepped one stage ahead, since the
+// x-gradient of stage k+1 needs it, and each old-point value is read before
+// its stage's copy overwrites it.
+__device__ __forceinline__ void accept_pass(
+    int N, int64_t ld, double alpha, bool has_r, const double* __restrict__ mu_,
+    const double* __restrict__ nul_, const double* __restrict__ nuu_,
+    double* __restrict__ lam_, double* __restrict__ pil_, double* __restrict__ piu_,
+    const double* __restrict__ r_, double* __restrict__ glu_, double* __restrict__ glx_,
+    const double* __restrict__ ut_, double* __restrict__ u_, double* __restrict__ du_,
+    const double* __restrict__ xt_, double* __restrict__ x_, const double* __restrict__ ta_,
+    double* __restrict__ ea_, const double* __restrict__ tb_, double* __restrict__ eb_,
+    const double* __restrict__ tg_, double* __restrict__ eg_, const double* __restrict__ tq_,
+    double* __restrict__ eq_) {
+  const double ialpha = 1.0 / alpha;  // alpha is a power of two: exact
+  double lam = lam_[0] + alpha * (mu_[0] - lam_[0]);
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    lam_[o] = lam;
+    const double pil = pil_[o] + alpha * (nul_[o] - pil_[o]);
+    const double piu = piu_[o] + alpha * (nuu_[o] - piu_[o]);
+    pil_[o] = pil;
+    piu_[o] = piu;
+    double glu = -lam * eb_[o] - pil + piu;
+    if (has_r) glu += r_[o];
+    double gx, lam_n = 0.0;
+    if (k + 1 < N) {
+      lam_n = lam_[o + ld] + alpha * (mu_[o + ld] - lam_[o + ld]);
+      gx = eq_[o + ld] - lam_n * ea_[o + ld] + lam;
+    } else {
+      gx = eq_[o + ld] + lam;
+    }
+    glu_[o] = glu;
+    glx_[o + ld] = gx;
+    const double un = ut_[o];
+    du_[o] = (un - u_[o]) * ialpha;
+    u_[o] = un;
+    x_[o + ld] = xt_[o + ld];
+    ea_[o] = ta_[o];
+    eb_[o] = tb_[o];
+    eg_[o] = tg_[o];
+    eq_[o + ld] = tq_[o + ld];
+    lam = lam_n;
+  }
 }
 
 // Armijo test of the evaluated trial point.  Returns 0 when the step was
@@ -345,36 +495,11 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
     return 2;
   }
   const double alpha = s.alpha;
-  // step in the multipliers; old-point Lagrangian gradient at the new multipliers
-  for (int k = 0; k < N; ++k) {
-    w(LAM, k) = w(LAM, k) + alpha * (w(MU, k) - w(LAM, k));
-    w(PIL, k) = w(PIL, k) + alpha * (w(NUL, k) - w(PIL, k));
-    w(PIU, k) = w(PIU, k) + alpha * (w(NUU, k) - w(PIU, k));
-  }
-  for (int k = 0; k < N; ++k) {
-    const double lam = w(LAM, k);
-    w(GLU, k) = -lam * w(EB, k) - w(PIL, k) + w(PIU, k);
-    if (c.Ru != 0.0) w(GLU, k) += w(QR, k);   // r at the old point
-    double gx;
-    if (k + 1 < N)
-      gx = w(EQ, k + 1) - w(LAM, k + 1) * w(EA, k + 1) + lam;
-    else
-      gx = w(EQ, N) + lam;
-    w(GLX, k + 1) = gx;
-  }
-  // accept the trial point and its evaluation; the step actually taken
-  // (after the bound clip) is what BFGS sees
-  const double ialpha = 1.0 / alpha;  // alpha is a power of two: exact
-  for (int k = 0; k < N; ++k) {
-    const double un = w(UT, k);
-    w(DU, k) = (un - w(U, k)) * ialpha;
-    w(U, k) = un;
-    w(X, k + 1) = w(XT, k + 1);
-    w(EA, k) = w(TA, k);
-    w(EB, k) = w(TB, k);
-    w(EG, k) = w(TG, k);
-    w(EQ, k + 1) = w(TQ, k + 1);
-  }
+  accept_pass(N, w.ld, alpha, c.Ru != 0.0, ws_col(w, MU), ws_col(w, NUL), ws_col(w, NUU),
+              ws_col(w, LAM), ws_col(w, PIL), ws_col(w, PIU), ws_col(w, QR), ws_col(w, GLU),
+              ws_col(w, GLX), ws_col(w, UT), ws_col(w, U), ws_col(w, DU), ws_col(w, XT),
+              ws_col(w, X), ws_col(w, TA), ws_col(w, EA), ws_col(w, TB), ws_col(w, EB),
+              ws_col(w, TG), ws_col(w, EG), ws_col(w, TQ), ws_col(w, EQ));
   w(EPR, 0) = w(TPR, 0);
   w(EPR, 1) = w(TPR, 1);
   s.f = s.ft;
