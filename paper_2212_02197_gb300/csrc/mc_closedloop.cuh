@@ -156,6 +156,27 @@ __device__ __forceinline__ bool nmpc_sample_body(const DevModel& m, const DevCtr
   return true;
 }
 
+// The receding-horizon shift of the warm start and of the final evaluation
+// by one interval, the last entry duplicated (columns as in the SQP passes).
+__device__ __forceinline__ void shift_pass(int N, int64_t ld, double* __restrict__ u_,
+                                           double* __restrict__ x1_, double* __restrict__ lam_,
+                                           double* __restrict__ pil_, double* __restrict__ piu_,
+                                           double* __restrict__ ea_, double* __restrict__ eb_,
+                                           double* __restrict__ eg_) {
+#pragma unroll 2
+  for (int k = 0; k < N - 1; ++k) {
+    const int64_t o = k * ld;
+    u_[o] = u_[o + ld];
+    x1_[o] = x1_[o + ld];
+    lam_[o] = lam_[o + ld];
+    pil_[o] = pil_[o + ld];
+    piu_[o] = piu_[o + ld];
+    ea_[o] = ea_[o + ld];
+    eb_[o] = eb_[o + ld];
+    eg_[o] = eg_[o + ld];
+  }
+}
+
 // After the OCP of sample i: count it, apply u_0, shift the warm start (and
 // the final evaluation) one interval, simulate the plant to t_{i+1}.
 template <class R>
@@ -171,16 +192,8 @@ __device__ __forceinline__ void nmpc_apply_body(const DevModel& m, const DevCtrl
   T.out.cnt[5] += si.qp_iters;
   T.out.cnt[7] += si.qp_fail;
   const double F = w(U, 0) * c.Fconv;
-  for (int k = 0; k < N - 1; ++k) {
-    w(U, k) = w(U, k + 1);
-    w(X, k + 1) = w(X, k + 2);
-    w(LAM, k) = w(LAM, k + 1);
-    w(PIL, k) = w(PIL, k + 1);
-    w(PIU, k) = w(PIU, k + 1);
-    w(EA, k) = w(EA, k + 1);
-    w(EB, k) = w(EB, k + 1);
-    w(EG, k) = w(EG, k + 1);
-  }
+  shift_pass(N, w.ld, ws_col(w, U), ws_col(w, X) + w.ld, ws_col(w, LAM), ws_col(w, PIL),
+             ws_col(w, PIU), ws_col(w, EA), ws_col(w, EB), ws_col(w, EG));
   plant_interval<R>(m, T.tp, T.j, T.i, F, T.n, nzc, nz_ld);
   T.F_prev = F;
   T.i++;

@@ -229,17 +229,16 @@ MC_HD int as_multipliers(int N, int64_t ld, uint64_t fixed, uint64_t lo, bool ha
   return worst;
 }
 
-MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
-  const int64_t ld = w.ld;
-  const double *A_ = ws_col(w, EA), *B_ = ws_col(w, EB), *b_ = ws_col(w, EG),
-               *q_ = ws_col(w, EQ), *r_ = ws_col(w, QR), *Wxx = ws_col(w, WXX),
-               *Wxu = ws_col(w, WXU), *Wuu = ws_col(w, WUU), *lb_ = ws_col(w, LB),
-               *ub_ = ws_col(w, UB);
-  double *du_ = ws_col(w, DU), *dx_ = ws_col(w, DX), *mu_ = ws_col(w, MU),
-         *nul_ = ws_col(w, NUL), *nuu_ = ws_col(w, NUU), *P_ = ws_col(w, RP),
-         *p_ = ws_col(w, RPP), *K_ = ws_col(w, RK), *kf_ = ws_col(w, RKF), *z_ = ws_col(w, RZ);
-  uint64_t lo = 0, up = 0;
+// Working set at the start (bounds active at the current iterate, du on them)
+// and the scale of the multiplier test.
+MC_HD double as_init(int N, int64_t ld, bool has_r, const double* __restrict__ lb_,
+                     const double* __restrict__ ub_, const double* __restrict__ q_,
+                     const double* __restrict__ r_, double* __restrict__ du_, uint64_t& lo,
+                     uint64_t& up) {
+  lo = 0;
+  up = 0;
   double gscale = 1.0;
+#pragma unroll 2
   for (int k = 0; k < N; ++k) {
     const int64_t o = k * ld;
     const double lb = lb_[o], ub = ub_[o];
@@ -255,6 +254,41 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
     gscale = fmax(gscale, fabs(q_[o + ld]));
     if (has_r) gscale = fmax(gscale, fabs(r_[o]));
   }
+  return gscale;
+}
+
+// Bound multipliers from stationarity in du at the final working set.
+MC_HD void as_bound_multipliers(int N, int64_t ld, uint64_t lo, uint64_t up, bool has_r,
+                                const double* __restrict__ B_, const double* __restrict__ r_,
+                                const double* __restrict__ Wxu, const double* __restrict__ Wuu,
+                                const double* __restrict__ du_, const double* __restrict__ dx_,
+                                const double* __restrict__ mu_, double* __restrict__ nul_,
+                                double* __restrict__ nuu_) {
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    double nl = 0.0, nu = 0.0;
+    if (((lo | up) >> k) & 1ull) {
+      const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
+      const double v = Wuu[o] * du_[o] + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
+      if ((lo >> k) & 1ull) nl = v; else nu = -v;
+    }
+    nul_[o] = nl;
+    nuu_[o] = nu;
+  }
+}
+
+MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
+  const int64_t ld = w.ld;
+  const double *A_ = ws_col(w, EA), *B_ = ws_col(w, EB), *b_ = ws_col(w, EG),
+               *q_ = ws_col(w, EQ), *r_ = ws_col(w, QR), *Wxx = ws_col(w, WXX),
+               *Wxu = ws_col(w, WXU), *Wuu = ws_col(w, WUU), *lb_ = ws_col(w, LB),
+               *ub_ = ws_col(w, UB);
+  double *du_ = ws_col(w, DU), *dx_ = ws_col(w, DX), *mu_ = ws_col(w, MU),
+         *nul_ = ws_col(w, NUL), *nuu_ = ws_col(w, NUU), *P_ = ws_col(w, RP),
+         *p_ = ws_col(w, RPP), *K_ = ws_col(w, RK), *kf_ = ws_col(w, RKF), *z_ = ws_col(w, RZ);
+  uint64_t lo, up;
+  const double gscale = as_init(N, ld, has_r, lb_, ub_, q_, r_, du_, lo, up);
   const double mult_tol = 1e-13 * gscale;
 
   QpResult res{0, 1};
@@ -296,18 +330,7 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
     lo &= ~(1ull << worst);
     up &= ~(1ull << worst);
   }
-  // bound multipliers from stationarity in du
-  for (int k = 0; k < N; ++k) {
-    const int64_t o = k * ld;
-    double nl = 0.0, nu = 0.0;
-    if (((lo | up) >> k) & 1ull) {
-      const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
-      const double v = Wuu[o] * du_[o] + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
-      if ((lo >> k) & 1ull) nl = v; else nu = -v;
-    }
-    nul_[o] = nl;
-    nuu_[o] = nu;
-  }
+  as_bound_multipliers(N, ld, lo, up, has_r, B_, r_, Wxu, Wuu, du_, dx_, mu_, nul_, nuu_);
   dx_[0] = 0.0;
   return res;
 }
