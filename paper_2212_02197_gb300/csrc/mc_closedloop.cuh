@@ -314,16 +314,15 @@ __device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, 
     const int aa = trial ? TA : EA, ba = trial ? TB : EB, ga = trial ? TG : EG;
     const Ws wo{w.p + (o - lane), w.ld, w.N1};
     const double xk = (k == 0) ? wo(X, 0) : wo(xa, k);
-    double A, B, g, xpr, Ppr;
-    shoot_interval<R>(m, c, tab.EaR[o], xk, wo(ua, k), wo(xa, k + 1), xs, ixs, A, B, g, k == 0,
-                      wo(PIN, 0), xpr, Ppr);
-    wo(aa, k) = A;
-    wo(ba, k) = B;
-    wo(ga, k) = g;
+    const Shot r = shoot_interval<R>(m, c, tab.EaR[o], xk, wo(ua, k), wo(xa, k + 1), xs, ixs,
+                                     k == 0, wo(PIN, 0));
+    wo(aa, k) = r.A;
+    wo(ba, k) = r.B;
+    wo(ga, k) = r.g;
     if (k == 0) {
       const int pa = trial ? TPR : EPR;
-      wo(pa, 0) = xpr;
-      wo(pa, 1) = Ppr;
+      wo(pa, 0) = r.xpr;
+      wo(pa, 1) = r.Ppr;
     }
   }
   __syncwarp();  // the shot intervals are visible to their owners

@@ -54,16 +54,18 @@ __device__ __forceinline__ void model1_d2(const DevModel& m, double EaR, double 
 // One shooting interval (n_rk4 RK4 steps) with first- and second-order
 // forward sensitivities of the end state with respect to x0 and v, obtained
 // by differentiating every RK4 stage twice.
-__device__ __noinline__ void rk4_interval_d2(const DevModel& m, double EaR, int n_rk4, double Ts,
-                                             double x0, double v, double Fconv, double& xF,
-                                             double& a, double& b, double& aa, double& ab,
-                                             double& bb) {
+// The results come back by value (references would put the caller's variables
+// in local memory).
+struct D2 {
+  double xF, a, b, aa, ab, bb;
+};
+
+__device__ __noinline__ D2 rk4_interval_d2(const DevModel& m, double EaR, int n_rk4, double Ts,
+                                           double x0, double v, double Fconv) {
   const double h = Ts / (double)n_rk4;
   const double F = v * Fconv;
   double x = x0;
-  a = 1.0;
-  b = 0.0;
-  aa = ab = bb = 0.0;
+  double a = 1.0, b = 0.0, aa = 0.0, ab = 0.0, bb = 0.0;
   for (int s = 0; s < n_rk4; ++s) {
     double Kx = 0, Ka = 0, Kb = 0, Kaa = 0, Kab = 0, Kbb = 0;        // previous stage
     double Sx = 0, Sa = 0, Sb = 0, Saa = 0, Sab = 0, Sbb = 0;        // weighted sums
@@ -96,7 +98,7 @@ __device__ __noinline__ void rk4_interval_d2(const DevModel& m, double EaR, int 
     ab += h6 * Sab;
     bb += h6 * Sbb;
   }
-  xF = x;
+  return D2{x, a, b, aa, ab, bb};
 }
 
 // du_0 / d(x_0, Q_z, R_u, Q_n) at the KKT point in (U, X, LAM, PIL, PIU) with
@@ -120,9 +122,8 @@ __device__ bool ocp_sens(const DevModel& m, const DevCtrl& c, double EaR, int N,
   }
   for (int k = N - 1; k >= 0; --k) {
     const double xk = w(X, k), uk = w(U, k), lam = w(LAM, k);
-    double xF, a, b, aa, ab, bb;
-    rk4_interval_d2(m, EaR, c.n_rk4, Ts, xk * xs, uk, c.Fconv, xF, a, b, aa, ab, bb);
-    const double A = a, B = b / xs, Fxx = aa * xs, Fxu = ab, Fuu = bb / xs;
+    const D2 d2 = rk4_interval_d2(m, EaR, c.n_rk4, Ts, xk * xs, uk, c.Fconv);
+    const double A = d2.a, B = d2.b / xs, Fxx = d2.aa * xs, Fxu = d2.ab, Fuu = d2.bb / xs;
     const double Huu = 2.0 * Ts * c.Ru - lam * Fuu;
     const double Hxu = -lam * Fxu;
     const double Hxx = 2.0 * Ts * c.Qz * sz * sz - lam * Fxx;

@@ -206,12 +206,15 @@ MC_HD int as_forward(int N, int64_t ld, uint64_t fixed, const double* __restrict
 
 // At a subspace minimiser: du = z on the free stages, and the working-set
 // multipliers; returns the stage with the most negative one (-1: optimal).
+// The bound multipliers of the working set are written too (0 on free
+// stages): when no multiplier is negative they are the QP's.
 MC_HD int as_multipliers(int N, int64_t ld, uint64_t fixed, uint64_t lo, bool has_r,
                          double mult_tol, const double* __restrict__ B_,
                          const double* __restrict__ r_, const double* __restrict__ Wxu,
                          const double* __restrict__ Wuu, const double* __restrict__ z_,
                          const double* __restrict__ dx_, const double* __restrict__ mu_,
-                         double* __restrict__ du_) {
+                         double* __restrict__ du_, double* __restrict__ nul_,
+                         double* __restrict__ nuu_) {
   int worst = -1;
   double worst_val = -mult_tol;
 #pragma unroll 2
@@ -220,11 +223,17 @@ MC_HD int as_multipliers(int N, int64_t ld, uint64_t fixed, uint64_t lo, bool ha
     const bool f = (fixed >> k) & 1ull;
     const double du = f ? du_[o] : z_[o];
     du_[o] = du;
-    if (!f) continue;
-    const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
-    const double v = Wuu[o] * du + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
-    const double lam = ((lo >> k) & 1ull) ? v : -v;
-    if (lam < worst_val) { worst_val = lam; worst = k; }
+    double nl = 0.0, nu = 0.0;
+    if (f) {
+      const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
+      const double v = Wuu[o] * du + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
+      const bool at_lo = (lo >> k) & 1ull;
+      const double lam = at_lo ? v : -v;
+      if (lam < worst_val) { worst_val = lam; worst = k; }
+      if (at_lo) nl = v; else nu = -v;
+    }
+    nul_[o] = nl;
+    nuu_[o] = nu;
   }
   return worst;
 }
@@ -278,7 +287,10 @@ MC_HD void as_bound_multipliers(int N, int64_t ld, uint64_t lo, uint64_t up, boo
   }
 }
 
-MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
+// The active-set method from a given starting working set (lo, up), with du
+// already on the active bounds and gscale the scale of the multiplier test.
+MC_HD QpResult qp_active_set_from(const Ws& w, int N, bool has_r, int max_it, uint64_t lo,
+                                  uint64_t up, double gscale) {
   const int64_t ld = w.ld;
   const double *A_ = ws_col(w, EA), *B_ = ws_col(w, EB), *b_ = ws_col(w, EG),
                *q_ = ws_col(w, EQ), *r_ = ws_col(w, QR), *Wxx = ws_col(w, WXX),
@@ -287,8 +299,6 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
   double *du_ = ws_col(w, DU), *dx_ = ws_col(w, DX), *mu_ = ws_col(w, MU),
          *nul_ = ws_col(w, NUL), *nuu_ = ws_col(w, NUU), *P_ = ws_col(w, RP),
          *p_ = ws_col(w, RPP), *K_ = ws_col(w, RK), *kf_ = ws_col(w, RKF), *z_ = ws_col(w, RZ);
-  uint64_t lo, up;
-  const double gscale = as_init(N, ld, has_r, lb_, ub_, q_, r_, du_, lo, up);
   const double mult_tol = 1e-13 * gscale;
 
   QpResult res{0, 1};
@@ -322,7 +332,7 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
       continue;
     }
     const int worst = as_multipliers(N, ld, fixed, lo, has_r, mult_tol, B_, r_, Wxu, Wuu, z_,
-                                     dx_, mu_, du_);
+                                     dx_, mu_, du_, nul_, nuu_);
     if (worst < 0) {
       res.status = 0;
       break;
@@ -330,9 +340,20 @@ MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
     lo &= ~(1ull << worst);
     up &= ~(1ull << worst);
   }
-  as_bound_multipliers(N, ld, lo, up, has_r, B_, r_, Wxu, Wuu, du_, dx_, mu_, nul_, nuu_);
+  // the multiplier pass wrote the bound multipliers of an optimal working set;
+  // at the iteration limit they follow from the last one
+  if (res.status != 0)
+    as_bound_multipliers(N, ld, lo, up, has_r, B_, r_, Wxu, Wuu, du_, dx_, mu_, nul_, nuu_);
   dx_[0] = 0.0;
   return res;
+}
+
+// The active-set method started at the bounds active at the current iterate.
+MC_HD QpResult qp_active_set(const Ws& w, int N, bool has_r, int max_it) {
+  uint64_t lo, up;
+  const double gscale = as_init(N, w.ld, has_r, ws_col(w, LB), ws_col(w, UB), ws_col(w, EQ),
+                                ws_col(w, QR), ws_col(w, DU), lo, up);
+  return qp_active_set_from(w, N, has_r, max_it, lo, up, gscale);
 }
 
 // ---------------------------------------------------------------------------

@@ -31,7 +31,8 @@ struct SqpState {
   int N, max_it;      // horizon and iteration limit of this OCP
   int l;              // iteration counter
   int hv;             // halvings in the current line search
-  double f, ft, alpha, T0, DT0;
+  bool pt_ready;      // pt holds the trial point's penalty sigma^T |g|
+  double f, ft, pt, alpha, T0, DT0;
   SqpInfo info;
 };
 
@@ -42,19 +43,26 @@ struct SqpState {
 // one compiled body, so both give the same bits.
 // With cov (interval 0), the same RK4 stages also give the CD-EKF prediction
 // of the next sample from (x_0, P0) under this input: xpr = F_0 in K L and Ppr.
+// The results come back by value: a non-inlined function that wrote them
+// through references would force the caller's variables into local memory.
+struct Shot {
+  double A, B, g, xpr, Ppr;
+};
+
 template <class R>
-__device__ __noinline__ void shoot_interval(const DevModel& m, const DevCtrl& c, double EaR,
+__device__ __noinline__ Shot shoot_interval(const DevModel& m, const DevCtrl& c, double EaR,
                                             double xk, double uk, double xn, double xs,
-                                            double ixs, double& A, double& B, double& g,
-                                            bool cov, double P0, double& xpr, double& Ppr) {
+                                            double ixs, bool cov, double P0) {
   R Fn, a, b, P1 = 0;
   rk4_interval<R, true>(m, (R)EaR, c.n_rk4, (R)m.Ts, (R)(xk * xs), (R)uk, (R)c.Fconv, Fn, a,
                         b, cov, (R)P0, &P1);
-  A = (double)a;
-  B = (double)b * ixs;
-  g = (double)Fn * ixs - xn;
-  xpr = (double)Fn;
-  Ppr = (double)P1;
+  Shot r;
+  r.A = (double)a;
+  r.B = (double)b * ixs;
+  r.g = (double)Fn * ixs - xn;
+  r.xpr = (double)Fn;
+  r.Ppr = (double)P1;
+  return r;
 }
 
 // The objective's stage terms Q_z (z_k - zbar_k)^2 T_s, k = 1..N, and their
@@ -73,6 +81,25 @@ __device__ __forceinline__ double objective_pass(int N, int64_t ld, double Qz, d
     q_[o] = qf * dz;
   }
   return f;
+}
+
+// The same interval without the covariance: the static schedule's intervals
+// 1 .. N-1, which need no runtime test of the covariance flag in their RK4
+// steps.  Same operations on x, A and B as shoot_interval.
+template <class R>
+__device__ __noinline__ Shot shoot_interval_plain(const DevModel& m, const DevCtrl& c,
+                                                  double EaR, double xk, double uk, double xn,
+                                                  double xs, double ixs) {
+  R Fn, a, b;
+  rk4_interval<R, true>(m, (R)EaR, c.n_rk4, (R)m.Ts, (R)(xk * xs), (R)uk, (R)c.Fconv, Fn, a,
+                        b);
+  Shot r;
+  r.A = (double)a;
+  r.B = (double)b * ixs;
+  r.g = (double)Fn * ixs - xn;
+  r.xpr = 0.0;
+  r.Ppr = 0.0;
+  return r;
 }
 
 // Which intervals evaluate integrates.
@@ -130,16 +157,17 @@ __device__ __noinline__ double evaluate(const DevModel& m, const DevCtrl& c, dou
   for (int k = 0; k < N; ++k) {
     const double xn = w(x_arr, k + 1);
     if (rk_mode == kRkAll || (rk_mode == kRkEnds && (k == 0 || k == N - 1))) {
-      double A, B, g, xpr, Ppr;
-      shoot_interval<R>(m, c, EaR, xk, w(u_arr, k), xn, xs, ixs, A, B, g, k == 0, w(PIN, 0),
-                        xpr, Ppr);
-      w(a_arr, k) = A;
-      w(b_arr, k) = B;
-      w(g_arr, k) = g;
+      Shot r;
       if (k == 0) {
-        w(pr_arr, 0) = xpr;
-        w(pr_arr, 1) = Ppr;
+        r = shoot_interval<R>(m, c, EaR, xk, w(u_arr, k), xn, xs, ixs, true, w(PIN, 0));
+        w(pr_arr, 0) = r.xpr;
+        w(pr_arr, 1) = r.Ppr;
+      } else {
+        r = shoot_interval_plain<R>(m, c, EaR, xk, w(u_arr, k), xn, xs, ixs);
       }
+      w(a_arr, k) = r.A;
+      w(b_arr, k) = r.B;
+      w(g_arr, k) = r.g;
     }
     const double dz = xn * xs * m.iV - w(ZB, k + 1);
     f += c.Qz * dz * dz * m.Ts;
@@ -222,6 +250,7 @@ __device__ __forceinline__ void sqp_start(const DevModel& m, const DevCtrl& c, d
   s.max_it = max_it;
   s.l = 0;
   s.hv = 0;
+  s.pt_ready = false;
   s.alpha = 0.0;
   s.info = SqpInfo{};
   for (int k = 0; k <= N; ++k) {
@@ -258,15 +287,19 @@ __device__ __forceinline__ void check_pass(
     const double* __restrict__ lam_, const double* __restrict__ pil_,
     const double* __restrict__ piu_, const double* __restrict__ A_,
     const double* __restrict__ B_, const double* __restrict__ g_, const double* __restrict__ q_,
-    const double* __restrict__ r_, const double* __restrict__ du_,
+    const double* __restrict__ r_, double* __restrict__ du_,
     const double* __restrict__ dx_, const double* __restrict__ glu_,
     double* __restrict__ glx_, double* __restrict__ wxx_, double* __restrict__ wxu_,
     double* __restrict__ wuu_, const double* __restrict__ u_, double* __restrict__ lb_,
-    double* __restrict__ ub_, double& kg, double& ke, double& mult1, bool& pd) {
+    double* __restrict__ ub_, double& kg, double& ke, double& mult1, bool& pd, uint64_t& lo,
+    uint64_t& up, double& gscale) {
   kg = 0.0;
   ke = 0.0;
   mult1 = 0.0;
   pd = true;
+  lo = 0;
+  up = 0;
+  gscale = 1.0;
   double lam = lam_[0];
 #pragma unroll 2
   for (int k = 0; k < N; ++k) {
@@ -313,9 +346,23 @@ __device__ __forceinline__ void check_pass(
     }
     kg = fmax(kg, fmax(fabs(gu), fabs(gx)));
     ke = fmax(ke, fabs(g_[o]));
+    // the QP's bounds and starting working set (the bounds active at the
+    // current iterate, du on them), read after the BFGS step read du
     const double u = u_[o];
-    lb_[o] = vmin - u;
-    ub_[o] = vmax - u;
+    const double lb = vmin - u, ub = vmax - u;
+    lb_[o] = lb;
+    ub_[o] = ub;
+    double du0 = 0.0;
+    if (lb >= 0.0) {
+      lo |= 1ull << k;
+      du0 = lb;
+    } else if (ub <= 0.0) {
+      up |= 1ull << k;
+      du0 = ub;
+    }
+    du_[o] = du0;
+    gscale = fmax(gscale, fabs(q_[o + ld]));
+    if (has_r) gscale = fmax(gscale, fabs(r_[o]));
     lam = lam_n;
   }
 }
@@ -359,13 +406,14 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
   const bool has_r = (c.Ru != 0.0);
   if (has_r)  // input gradient r_k = 2 R_u (v_k - vbar_{k+1}) T_s at the current point
     for (int k = 0; k < N; ++k) w(QR, k) = c.r_scale * (w(U, k) - w(VB, k + 1));
-  double kg, ke, mult1;
+  double kg, ke, mult1, gscale;
   bool pd;
+  uint64_t lo, up;
   check_pass(N, ld, s.l > 0, s.alpha, has_r, c.vmin, c.vmax, ws_col(w, LAM), ws_col(w, PIL),
              ws_col(w, PIU), ws_col(w, EA), ws_col(w, EB), ws_col(w, EG), ws_col(w, EQ),
              ws_col(w, QR), ws_col(w, DU), ws_col(w, DX), ws_col(w, GLU), ws_col(w, GLX),
              ws_col(w, WXX), ws_col(w, WXU), ws_col(w, WUU), ws_col(w, U), ws_col(w, LB),
-             ws_col(w, UB), kg, ke, mult1, pd);
+             ws_col(w, UB), kg, ke, mult1, pd, lo, up, gscale);
   if (s.l > 0 && !pd) {
     // a block is not positive definite: reset all of them to the identity
     for (int k = 0; k <= N; ++k) {
@@ -389,9 +437,11 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
     return true;
   }
 
-  // QP subproblem at xi^[l] (bounds LB, UB from the first pass)
-  const QpResult qr = (c.qp_solver == 1) ? qp_ipm(w, N, has_r, c.ip_max_it, c.ip_tol)
-                                         : qp_active_set(w, N, has_r, 10 * N + 20);
+  // QP subproblem at xi^[l] (bounds LB, UB and the starting working set from
+  // the first pass)
+  const QpResult qr = (c.qp_solver == 1)
+                          ? qp_ipm(w, N, has_r, c.ip_max_it, c.ip_tol)
+                          : qp_active_set_from(w, N, has_r, 10 * N + 20, lo, up, gscale);
   s.info.qp_iters += qr.iters;
   if (qr.status != 0) s.info.qp_fail++;
   s.info.iters++;
@@ -412,15 +462,41 @@ template <class R>
 __device__ __forceinline__ void sqp_eval_trial(const DevModel& m, const DevCtrl& c, double EaR,
                                                const Ws& w, SqpState& s) {
   s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ, kRkAll);
+  s.pt_ready = false;
   s.info.ls_trials++;
 }
 
+// The trial point's objective terms and q_k, and its penalty sigma^T |g| (the
+// same sums, in the same order, as the objective pass and the Armijo test).
+__device__ __forceinline__ void trial_objective_pass(
+    int N, int64_t ld, double Qz, double Ts, double xs, double iV, double qf,
+    const double* __restrict__ x_, const double* __restrict__ zb_, double* __restrict__ q_,
+    const double* __restrict__ sig_, const double* __restrict__ g_, double& f, double& pt) {
+  f = 0.0;
+  pt = 0.0;
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const int64_t o = k * ld;
+    const double dz = x_[o + ld] * xs * iV - zb_[o + ld];
+    f += Qz * dz * dz * Ts;
+    q_[o + ld] = qf * dz;
+    pt += sig_[o] * fabs(g_[o]);
+  }
+}
+
 // The same trial evaluation after the warp has shot the intervals (the
-// persistent schedule's pool): only the objective and q_k are formed here.
+// persistent schedule's pool): only the objective, q_k and the penalty.
 template <class R>
 __device__ __forceinline__ void sqp_eval_trial_shot(const DevModel& m, const DevCtrl& c,
                                                     double EaR, const Ws& w, SqpState& s) {
-  s.ft = evaluate<R>(m, c, EaR, s.N, w, UT, XT, TA, TB, TG, TQ, kRkNone);
+  const double xs = c.x_scale;
+  const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
+  double f, pt;
+  trial_objective_pass(s.N, w.ld, c.Qz, m.Ts, xs, m.iV, qf, ws_col(w, XT), ws_col(w, ZB),
+                       ws_col(w, TQ), ws_col(w, SIG), ws_col(w, TG), f, pt);
+  s.ft = f + objective_extra(m, c, s.N, w, UT, XT, TQ);
+  s.pt = pt;
+  s.pt_ready = true;
   s.info.ls_trials++;
 }
 
@@ -483,7 +559,11 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
   const int N = s.N;
   const double c1 = 1e-4;
   double pt = 0.0;
-  for (int k = 0; k < N; ++k) pt += w(SIG, k) * fabs(w(TG, k));
+  if (s.pt_ready) {
+    pt = s.pt;
+  } else {
+    for (int k = 0; k < N; ++k) pt += w(SIG, k) * fabs(w(TG, k));
+  }
   if (!(s.ft + pt <= s.T0 + c1 * s.alpha * s.DT0)) {
     if (s.hv >= c.ls_max) {
       s.info.status = 2;
