@@ -90,7 +90,7 @@ def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st, w):
     elementary functions weighted by w (DFMA equivalents)."""
     N, nrk = cfg_ctrl["N"], cfg_ctrl["n_rk4"]
     K, nem = cfg_model["n_steps"], cfg_model["n_em"]
-    model1 = OPS_MODEL1 + w["exp_table"] + w["div"]
+    model1 = OPS_MODEL1 + w["exp_table"] + w.get("rcp", w["div"])
     per_interval = nrk * (4 * model1 + OPS_RK4_STAGE) + OPS_INTERVAL_EXTRA
     first_evals = n_traj * N + (st["n_ocp"] - n_traj) * min(N, 2)   # warm starts reuse N-2
     ops = (first_evals + st["ls_trials"] * N) * per_interval
@@ -139,7 +139,7 @@ def measured_peaks():
         return peaks.measure(), "measured"
     except Exception as e:  # pragma: no cover
         return {"fp64_tflops": PEAK_NOMINAL_TFLOPS, "fp32_tflops": None,
-                "weights_dfma": {k: 1.0 for k in ("exp_table", "exp_lib", "div", "log",
+                "weights_dfma": {k: 1.0 for k in ("exp_table", "exp_lib", "div", "rcp", "log",
                                                   "sqrt", "sincospi")},
                 "error": str(e)}, "nominal (the probe failed; functions weighted 1)"
 

@@ -314,16 +314,24 @@ mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t pre
                    double* out_host, double* meas_host);
 
 /* The FP64 exponential every rate-law evaluation of the simulation uses
- * (k = k0 exp(-(E_a/R)/T), Eq. (CSTR)): y = e^x for n values, host arrays.
- * Tang's table-driven method; within about 1 ulp of the exact value. */
+ * (k = k0 exp(-(E_a/R)/T) = exp(log k0 - (E_a/R)/T), Eq. (CSTR)): y = e^x for
+ * n values, host arrays.  Tang's table-driven method; within about 1 ulp of
+ * the exact value. */
 mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host);
+
+/* The FP64 reciprocal the one-state rate law takes of the temperature
+ * (1/T in (E_a/R)/T and in dr/dT, Sec. VI): y = 1/x for n values, host
+ * arrays.  Two Newton-Raphson steps on the hardware's approximate
+ * reciprocal; within about 1 ulp of the exact value for normal x, the
+ * approximation's own value (exact) for zeros, infinities and NaN. */
+mc_status mc_rcp_batch(const double* x_host, int64_t n, double* out_host);
 
 /* Throughput probe of one arithmetic pipe on the current device, for the
  * roofline of the simulation kernels (the paper has no counterpart: its
  * timings are wall-clock on CPU cores).  kind: 0 FP64 fma chain, 1 fma + add,
  * 2 the rate law's table-driven exp, 3 the library exp, 4 FP64 division,
  * 5 log, 6 sqrt, 7 sincospi, 8 FP32 fma chain, 9 fma + expf, 10 FP32 fma +
- * add.  One launch of 16 four-warp blocks per SM, every thread with 8
+ * add, 11 the rate law's Newton-refined reciprocal.  One launch of 16 four-warp blocks per SM, every thread with 8
  * independent chains of `iters` steps (1 .. 2^30).  *ms_out receives the
  * launch's device time (CUDA events, after a short warm-up launch) and
  * *steps_out the number of chain steps it ran, so steps / time is the

@@ -273,9 +273,10 @@ __global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1
   if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
 }
 
-__global__ void k_exp(const double* __restrict__ x, int64_t n, double* __restrict__ y) {
+template <bool kRcp>
+__global__ void k_elementary(const double* __restrict__ x, int64_t n, double* __restrict__ y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = expr(x[i]);
+  if (i < n) y[i] = kRcp ? rcp_newton(x[i]) : expr(x[i]);
 }
 
 __global__ void k_noise(DevModel m, uint32_t j, int64_t k0, int64_t nk, int precision,
@@ -599,6 +600,7 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   m->bV = mm->beta * mm->V;
   m->ib2 = 2.0 * m->ib;
   m->key0 = (uint32_t)seed; m->key1 = (uint32_t)(seed >> 32);
+  m->lnk0 = std::log(mm->k0);   // -inf for k0 = 0: the rate vanishes
   m->hEM = mm->Ts / (double)mm->n_em;
   m->sqhEM = std::sqrt(m->hEM);
   // first sample index of each set-point segment: the smallest i >= 0 with
@@ -1349,22 +1351,33 @@ mc_status mc_noise(uint64_t seed, int64_t j, int64_t k0, int64_t nk, int32_t pre
   return s;
 }
 
-mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host) {
+static mc_status elementary_batch(const char* name, bool rcp, const double* x_host, int64_t n,
+                                  double* out_host) {
   if (n < 0 || (n > 0 && (!x_host || !out_host)))
-    return fail(nullptr, MC_EINVAL, "mc_exp_batch: bad arguments");
+    return fail(nullptr, MC_EINVAL, std::string(name) + ": bad arguments");
   if (n == 0) return MC_OK;
   double *dx = nullptr, *dy = nullptr;
   mc_status s = MC_OK;
   if (!to_dev<double>(&dx, x_host, n) || !to_dev<double>(&dy, nullptr, n)) {
-    s = fail(nullptr, MC_ENOMEM, "mc_exp_batch: allocation");
+    s = fail(nullptr, MC_ENOMEM, std::string(name) + ": allocation");
   } else {
-    k_exp<<<(unsigned)((n + 255) / 256), 256>>>(dx, n, dy);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (rcp) k_elementary<true><<<grid, 256>>>(dx, n, dy);
+    else k_elementary<false><<<grid, 256>>>(dx, n, dy);
     const cudaError_t e = cudaMemcpy(out_host, dy, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) s = cuda_fail(nullptr, e, "mc_exp_batch");
+    if (e != cudaSuccess) s = cuda_fail(nullptr, e, name);
   }
   cudaFree(dx);
   cudaFree(dy);
   return s;
+}
+
+mc_status mc_exp_batch(const double* x_host, int64_t n, double* out_host) {
+  return elementary_batch("mc_exp_batch", false, x_host, n, out_host);
+}
+
+mc_status mc_rcp_batch(const double* x_host, int64_t n, double* out_host) {
+  return elementary_batch("mc_rcp_batch", true, x_host, n, out_host);
 }
 
 mc_status mc_pipe_probe(int32_t kind, int64_t iters, double* ms_out, double* steps_out) {
@@ -1396,6 +1409,7 @@ mc_status mc_pipe_probe(int32_t kind, int64_t iters, double* ms_out, double* ste
       case kProbeSincos: k_pipe_probe<kProbeSincos><<<blocks, 128>>>(it, 1.0, out); break;
       case kProbeFfma: k_pipe_probe<kProbeFfma><<<blocks, 128>>>(it, 1.0, out); break;
       case kProbeExpf: k_pipe_probe<kProbeExpf><<<blocks, 128>>>(it, 1.0, out); break;
+      case kProbeRcp: k_pipe_probe<kProbeRcp><<<blocks, 128>>>(it, 1.0, out); break;
       default: k_pipe_probe<kProbeNoneF><<<blocks, 128>>>(it, 1.0, out); break;
     }
   };

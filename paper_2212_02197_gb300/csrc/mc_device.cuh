@@ -34,6 +34,7 @@ struct DevModel {
   double rw0, rw1, bV, ib2;  // one-state rate law: ib (cB_in + 2 cA_in), 4 ib^2,
                             // beta V, 2 ib
   uint32_t key0, key1;
+  double lnk0;          // log k0: the rate constant as one exp, k0 e^{-g} = e^{log k0 - g}
   int sp_step[kMaxSp];  // first sample i with t0 + i Ts >= sp_time[s] (set-point segments)
   double hEM, sqhEM;    // Euler-Maruyama step Ts / N_s and its square root
 };
@@ -286,6 +287,23 @@ __device__ __forceinline__ double exp_table(double x) {
 }
 
 __device__ __forceinline__ double expr(double x) { return exp_table(x); }
+
+// 1/x by Newton-Raphson refinement of the hardware's approximate FP64
+// reciprocal: y <- y + y (1 - x y) twice, each step doubling the correct bits
+// of the approximation, to within about 1 ulp of 1/x.  Zeros, infinities and
+// NaN (and denormals, which the approximation flushes) keep the approximate
+// value, which for them is already 1/x; the test is on the integer pipe.
+__device__ __forceinline__ double rcp_newton(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const int ex = __double2hiint(x) & 0x7ff00000;
+  if (ex == 0 || ex == 0x7ff00000) return y;
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ float rcp_newton(float x) { return 1.0f / x; }
 __device__ __forceinline__ float expr(float x) { return expf(x); }
 
 template <class R>
@@ -317,18 +335,22 @@ __device__ __forceinline__ void em_step(const DevModel& m, R EaR, R T_in, R n[3]
 //   f = F d + beta V r,
 //   dr/dc_T = r g / c_T - k (c_B + 2 c_A) / beta,
 //   df/dx = -F / V + beta dr/dc_T,
-// where (c_B + 2 c_A) / beta = rw0 + rw1 d is affine in d.  Written this way
-// the evaluation takes 15 FP64 operations besides the exp and the reciprocal
-// (and one, F / V, that stays the same over an interval).
+// where (c_B + 2 c_A) / beta = rw0 + rw1 d is affine in d.  Every rounding is
+// written out (fma where a product meets a sum), so that the compiler has no
+// contraction to choose and every function that inlines the model (the
+// schedules' shooting functions) rounds alike.  Written this way the
+// evaluation takes 15 FP64 operations besides the exp and the reciprocal (and
+// one, F / V, that stays the same over an interval); the reciprocal is
+// rcp_newton's and k0 enters the exponent as log k0.
 template <class R>
 __device__ __forceinline__ void model1(const DevModel& m, R EaR, R x, R F, R& f, R& fx,
                                        R& fF) {
   const R iV = (R)m.iV, ib = (R)m.ib;
   const R cT = x * iV;
-  const R d = (R)m.T_in - cT;
-  const R iT = (R)1 / cT;
+  const R d = fma(-x, iV, (R)m.T_in);
+  const R iT = rcp_newton(cT);
   const R g = EaR * iT;
-  const R k = (R)m.k0 * expr(-g);
+  const R k = expr(fma(-EaR, iT, (R)m.lnk0));
   const R cA = fma(d, ib, (R)m.cA_in);
   const R cB = fma(d, (R)m.ib2, (R)m.cB_in);
   const R r = k * (cA * cB);
@@ -339,6 +361,17 @@ __device__ __forceinline__ void model1(const DevModel& m, R EaR, R x, R F, R& f,
   fF = d;
 }
 
+// Sums whose operands may be products, rounded as written: the compiler never
+// merges these into a multiply-add.
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// The RK4 weighted sum k1 + 2 k2 + 2 k3 + k4, every rounding written out.
+template <class R>
+__device__ __forceinline__ R rk4_sum(R k1, R k2, R k3, R k4) {
+  return add_rn(fma((R)2, k3, fma((R)2, k2, k1)), k4);
+}
+
 // One shooting interval: n_rk4 classical RK4 steps over Ts from x0 (K L) with
 // flow F = v Fconv, and the forward sensitivities a = dx/dx0, B = dx/dv.
 // The RK4 stages propagate b = dx/dF, whose forcing is df/dF itself; B is
@@ -346,7 +379,8 @@ __device__ __forceinline__ void model1(const DevModel& m, R EaR, R x, R F, R& f,
 // With cov, the same stages also carry the CD-EKF covariance of Eq.
 // (predictionEquations), dP/dt = 2 (df/dx) P + (F sigma_T)^2, from P0 into
 // P1: xF and P1 are then the CD-EKF prediction, RK4 on (x, P) over one sample
-// from (x0, P0) under this input.
+// from (x0, P0) under this input.  As in model1, every rounding is written
+// out.
 template <class R, bool kSens>
 __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4, R Ts, R x0,
                                              R v, R Fconv, R& xF, R& A, R& B,
@@ -360,28 +394,28 @@ __device__ __forceinline__ void rk4_interval(const DevModel& m, R EaR, int n_rk4
   for (int s = 0; s < n_rk4; ++s) {
     R f1, fx1, fF1, f2, fx2, fF2, f3, fx3, fF3, f4, fx4, fF4;
     model1<R>(m, EaR, x, F, f1, fx1, fF1);
-    const R x2 = x + hh * f1;
+    const R x2 = fma(hh, f1, x);
     model1<R>(m, EaR, x2, F, f2, fx2, fF2);
-    const R x3 = x + hh * f2;
+    const R x3 = fma(hh, f2, x);
     model1<R>(m, EaR, x3, F, f3, fx3, fF3);
-    const R x4 = x + h * f3;
+    const R x4 = fma(h, f3, x);
     model1<R>(m, EaR, x4, F, f4, fx4, fF4);
     if (kSens) {
       const R a1 = fx1 * a, b1 = fma(fx1, b, fF1);
       const R a2 = fx2 * fma(hh, a1, a), b2 = fma(fx2, fma(hh, b1, b), fF2);
       const R a3 = fx3 * fma(hh, a2, a), b3 = fma(fx3, fma(hh, b2, b), fF3);
       const R a4 = fx4 * fma(h, a3, a), b4 = fma(fx4, fma(h, b3, b), fF4);
-      a = a + h6 * (a1 + (R)2 * a2 + (R)2 * a3 + a4);
-      b = b + h6 * (b1 + (R)2 * b2 + (R)2 * b3 + b4);
+      a = fma(h6, rk4_sum(a1, a2, a3, a4), a);
+      b = fma(h6, rk4_sum(b1, b2, b3, b4), b);
     }
     if (cov) {
-      const R p1 = (R)2 * fx1 * Ps + q;
-      const R p2 = (R)2 * fx2 * (Ps + hh * p1) + q;
-      const R p3 = (R)2 * fx3 * (Ps + hh * p2) + q;
-      const R p4 = (R)2 * fx4 * (Ps + h * p3) + q;
-      Ps = Ps + h6 * (p1 + (R)2 * p2 + (R)2 * p3 + p4);
+      const R p1 = fma((R)2 * fx1, Ps, q);
+      const R p2 = fma((R)2 * fx2, fma(hh, p1, Ps), q);
+      const R p3 = fma((R)2 * fx3, fma(hh, p2, Ps), q);
+      const R p4 = fma((R)2 * fx4, fma(h, p3, Ps), q);
+      Ps = fma(h6, rk4_sum(p1, p2, p3, p4), Ps);
     }
-    x = x + h6 * (f1 + (R)2 * f2 + (R)2 * f3 + f4);
+    x = fma(h6, rk4_sum(f1, f2, f3, f4), x);
   }
   xF = x;
   A = a;

@@ -3,7 +3,8 @@
 // pipe the FP64 path is bound by), FP32 fused multiply-adds, and the FP64
 // elementary operations of the rate law, the CD-EKF and the noise transform
 // (exp -- the kernel's own table-driven one and the library's -- division,
-// log, sqrt, sincospi) and FP32 expf.
+// the rate law's Newton-refined reciprocal, log, sqrt, sincospi) and FP32
+// expf.
 //
 // Every thread runs kChains independent chains for `iters` iterations.  Each
 // chain step is x = fma(x, a, b) (keeps x in a fixed range) followed by
@@ -30,7 +31,8 @@ enum PipeProbe : int {
   kProbeFfma = 8,   // FP32: x = fmaf(x, a, b)     (1 FFMA per step)
   kProbeExpf = 9,   // FP32: x = fmaf(x, a, b); y += expf(x)
   kProbeNoneF = 10, // FP32: x = fmaf(x, a, b); y += x
-  kNumProbes = 11
+  kProbeRcp = 11,   // ... y += rcp_newton(x), x near 300
+  kNumProbes = 12
 };
 
 constexpr int kChains = 8;
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(128) k_pipe_probe(int64_t iters, double seed,
                                                     double* __restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const double jitter = 1e-9 * (double)(t & 1023);
-  if constexpr (kKind >= kProbeFfma) {
+  if constexpr (kKind == kProbeFfma || kKind == kProbeExpf || kKind == kProbeNoneF) {
     float x[kChains], y[kChains];
     const float a = (float)(1.0 - 1e-7 * seed), b = (float)(-2.5e-6 * seed);
 #pragma unroll
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(128) k_pipe_probe(int64_t iters, double seed,
     double x[kChains], y[kChains];
     // x stays in the range the probed operation sees in the closed loop
     double x0 = -25.0, a = 1.0 - 1e-9 * seed, b = -2.5e-8 * seed;
-    if (kKind == kProbeDiv) { x0 = 300.0; b = 3e-7 * seed; }
+    if (kKind == kProbeDiv || kKind == kProbeRcp) { x0 = 300.0; b = 3e-7 * seed; }
     if (kKind == kProbeLog || kKind == kProbeSqrt || kKind == kProbeSincos) {
       x0 = 0.5; b = 5e-10 * seed;
     }
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(128) k_pipe_probe(int64_t iters, double seed,
         if constexpr (kKind == kProbeExpTab) y[i] += exp_table(x[i]);
         if constexpr (kKind == kProbeExpLib) y[i] += exp(x[i]);
         if constexpr (kKind == kProbeDiv) y[i] += 1.0 / x[i];
+        if constexpr (kKind == kProbeRcp) y[i] += rcp_newton(x[i]);
         if constexpr (kKind == kProbeLog) y[i] += log(x[i]);
         if constexpr (kKind == kProbeSqrt) y[i] += sqrt(x[i]);
         if constexpr (kKind == kProbeSincos) {

@@ -59,7 +59,7 @@ __device__ __noinline__ Shot shoot_interval(const DevModel& m, const DevCtrl& c,
   Shot r;
   r.A = (double)a;
   r.B = (double)b * ixs;
-  r.g = (double)Fn * ixs - xn;
+  r.g = fma((double)Fn, ixs, -xn);
   r.xpr = (double)Fn;
   r.Ppr = (double)P1;
   return r;
@@ -85,7 +85,9 @@ __device__ __forceinline__ double objective_pass(int N, int64_t ld, double Qz, d
 
 // The same interval without the covariance: the static schedule's intervals
 // 1 .. N-1, which need no runtime test of the covariance flag in their RK4
-// steps.  Same operations on x, A and B as shoot_interval.
+// steps.  Same operations on x, A and B as shoot_interval, and the same
+// bits: the model and the RK4 steps write out every rounding, so the two
+// compiled bodies leave the compiler no contraction to choose differently.
 template <class R>
 __device__ __noinline__ Shot shoot_interval_plain(const DevModel& m, const DevCtrl& c,
                                                   double EaR, double xk, double uk, double xn,
@@ -96,7 +98,7 @@ __device__ __noinline__ Shot shoot_interval_plain(const DevModel& m, const DevCt
   Shot r;
   r.A = (double)a;
   r.B = (double)b * ixs;
-  r.g = (double)Fn * ixs - xn;
+  r.g = fma((double)Fn, ixs, -xn);
   r.xpr = 0.0;
   r.Ppr = 0.0;
   return r;

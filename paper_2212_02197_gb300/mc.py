@@ -123,8 +123,9 @@ def lib():
             L.mc_ocp_sens_batch.argtypes = ([C.POINTER(McModel), C.POINTER(McController),
                                               C.c_int64] + [_dp] * 9 + [_ip])
             L.mc_ocp_sens_batch.restype = C.c_int
-            L.mc_exp_batch.argtypes = [_dp, C.c_int64, _dp]
-            L.mc_exp_batch.restype = C.c_int
+            for f in ("mc_exp_batch", "mc_rcp_batch"):
+                getattr(L, f).argtypes = [_dp, C.c_int64, _dp]
+                getattr(L, f).restype = C.c_int
             L.mc_pipe_probe.argtypes = [C.c_int32, C.c_int64, _dp, _dp]
             L.mc_pipe_probe.restype = C.c_int
             L.mc_set_pi_gains.argtypes = [H, C.c_double, C.c_double, C.c_double]
@@ -356,6 +357,14 @@ def exp_batch(x):
     x = np.ascontiguousarray(x, dtype=np.float64).ravel()
     y = np.empty_like(x)
     _check(lib().mc_exp_batch(_p(x), len(x), _p(y)))
+    return y
+
+
+def rcp_batch(x):
+    """The device FP64 reciprocal of the one-state rate law, elementwise on x."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.empty_like(x)
+    _check(lib().mc_rcp_batch(_p(x), len(x), _p(y)))
     return y
 
 

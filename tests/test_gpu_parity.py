@@ -104,6 +104,25 @@ def test_device_exp_within_two_ulp():
     assert y[-2] == np.inf and y[-1] == 0.0
 
 
+def test_device_reciprocal_within_one_ulp():
+    """The Newton-refined reciprocal of the one-state rate law against the
+    correctly rounded 1/x: temperatures the simulation meets (150..2000 K),
+    random magnitudes over the whole normal range with both signs, powers of
+    two (exact), and the special values (the approximation's own, exact)."""
+    rng = np.random.default_rng(11)
+    x = np.concatenate([np.linspace(150.0, 2000.0, 200001),
+                        rng.uniform(1.0, 2.0, 100000) * 2.0 ** rng.integers(-1000, 1000, 100000),
+                        -rng.uniform(1e-3, 1e3, 10000), 2.0 ** np.arange(-1000, 1001)])
+    y = mc.rcp_batch(x)
+    ref = 1.0 / x
+    ulp = np.abs(y - ref) / np.spacing(np.abs(ref))
+    assert ulp.max() <= 1.0, ulp.max()
+    assert np.all(y[-2001:] == ref[-2001:])   # powers of two are exact
+    sp = mc.rcp_batch(np.array([0.0, -0.0, np.inf, -np.inf, np.nan]))
+    assert sp[0] == np.inf and sp[1] == -np.inf and sp[2] == 0.0 and sp[3] == 0.0
+    assert np.signbit(sp[3]) and np.isnan(sp[4])
+
+
 @pytest.mark.parametrize("N", [1, 2, 5, 20, 31, 32, 33, 40, 60, 64])
 @pytest.mark.parametrize("solver", ["active_set", "ipm", "active_set_warp"])
 def test_qp_matches_oracle(N, solver):
