@@ -130,6 +130,31 @@ def nmpc_algorithmic_flops(cfg_model, cfg_ctrl, n_traj, st, w, opc):
     return flops
 
 
+def warp_trace_summary(h):
+    """Where the last persistent launch's time went, from its per-warp record
+    (mc_copy_warp_trace): the SMs' busy share of the launch (last warp end
+    minus first warp start on each SM, over the launch's span), the warps'
+    pool rounds, and the lanes holding a trajectory per round."""
+    import numpy as np
+
+    tr = h.warp_trace()
+    t0, t1, sm = tr["t_start_ns"], tr["t_end_ns"], tr["sm"]
+    span = float(t1.max() - t0.min())
+    busy = [float(t1[sm == q].max() - t0[sm == q].min()) for q in np.unique(sm)]
+    r = tr["rounds"].astype(float)
+    dur = (t1 - t0).astype(float)
+    slow = int(np.argmax(t1))
+    return {"warps": int(len(r)), "sms": int(len(busy)), "span_ms": span / 1e6,
+            "sm_busy_frac": float(np.mean(busy) / span),
+            "rounds_mean": float(r.mean()), "rounds_max": int(r.max()),
+            "lanes_per_round": float(tr["lane_rounds"].sum() / r.sum()),
+            "warp_ms_mean": float(dur.mean() / 1e6), "warp_ms_max": float(dur.max() / 1e6),
+            "last_warp": {"rounds": int(r[slow]), "ms": float(dur[slow] / 1e6),
+                          "us_per_round": float(dur[slow] / r[slow] / 1e3)},
+            "us_per_round_mean": float(np.mean(dur / r) / 1e3),
+            "corr_rounds_ms": float(np.corrcoef(r, dur)[0, 1])}
+
+
 def measured_peaks():
     """FP64/FP32 peaks and elementary-function costs measured on this device;
     falls back to the nominal FP64 peak and fixed weights if the probe fails."""
@@ -421,6 +446,8 @@ def main():
     else:
         roofline["achieved"], roofline["frac"] = pipe_tf, pipe_tf / peak
         roofline["work"] = roofline["pipe"]["work"]
+    if w["nmpc"].get("schedule") == "persistent" and w["nmpc"].get("nx_model", 1) != 3:
+        roofline["warp_trace"] = warp_trace_summary(h_n)
 
     def timed(handles, n, label_ranges=True):
         """Mean device ms of n timed runs of the handles (in order, one stream),
@@ -649,14 +676,18 @@ def main():
     # weights (Q_z, R_u, Q_n) at R_u = 0.2, Q_n = 1.0 (with the paper's
     # objective, R_u = Q_n = 0, the Q_z direction vanishes): implicit
     # derivatives of the OCPs' KKT points, forward-mode tangents of plant and
-    # CD-EKF, static schedule.  Checked by central differences where that is
+    # CD-EKF, on the study's schedule (persistent: the closed loop records each
+    # sample, then all lanes propagate the tangents through the records in
+    # step).  Checked by central differences where that is
     # meaningful: OCPs solved to 1e-7 (a looser SQP lags the exact solution
     # map), steps 1e-2 of each weight, 2,000 trajectories x 24 samples, over
     # the trajectories whose OCPs all converged.
     ngrad = None
     if (not args.no_grad and w["nmpc"]["precision"] == "fp64" and
             w["nmpc"].get("nx_model", 1) != 3):
-        cw = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+        cw = dict(w["nmpc"], Ru=0.2, Qn=1.0)
+        if cw.get("schedule") == "persistent" and tuned_tps:
+            cw["threads_per_sm"] = tuned_tps
         hg = mc.MonteCarlo(dict(w["model"], n_steps=min(24, w["model"]["n_steps"])), cw, j1,
                            w["seed"])
         for _ in range(max(1, args.warmup)):
@@ -676,19 +707,16 @@ def main():
         ng_st = hg.stats()
         hg.close()
         nf = min(2000, T)
-        cf = dict(cw, sqp_tol=1e-7, sqp_max_it=100)
+        # the persistent schedule keeps the warps busy past OCPs that need
+        # hundreds of iterations at this tolerance
+        cf = dict(cw, sqp_tol=1e-7, sqp_max_it=100, schedule="persistent")
+        cf.pop("threads_per_sm", None)
         hf = mc.MonteCarlo(dict(w["model"], n_steps=min(24, w["model"]["n_steps"])), cf, nf,
                            w["seed"])
         hf.nmpc_grad(stream)
         hf.sync()
         gf = hf.grad()
         okf = hf.counters()["n_ocp_failed"] == 0
-        hf.close()
-        # the perturbed runs on the persistent schedule (the same Phi bit for
-        # bit; its pool keeps the warps busy past OCPs that need hundreds of
-        # iterations at this tolerance)
-        hf = mc.MonteCarlo(dict(w["model"], n_steps=min(24, w["model"]["n_steps"])),
-                           dict(cf, schedule="persistent"), nf, w["seed"])
         fdr = {}
         for kk in ("Qz", "Ru", "Qn"):
             hk = 1e-2 * cf[kk]
@@ -723,6 +751,8 @@ def main():
                          "Q_n = 1), implicit OCP derivatives + forward-mode tangents",
                  "value": world * T / (ng_ms / 1e3), "unit": "trajectories/s (with tangents)",
                  "ms_per_step": ng_ms, "phi_mean": ng_st["phi_mean"],
+                 "schedule": cw.get("schedule", "static"),
+                 "threads_per_sm": cw.get("threads_per_sm"),
                  "grad_mean": ng_mean.tolist(),
                  "ocps_without_sensitivity": ng_st["qp_fail"],
                  "fd_check": {"trajectories": int(okf.sum()), "of": nf, "n_steps": 24,

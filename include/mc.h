@@ -212,6 +212,22 @@ mc_status mc_copy_phi(mc_handle* h, int64_t j0, int64_t n, double* dst, int dst_
 mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
                            int dst_is_device);
 
+/* Per-warp record of the last one-state NMPC launch on the persistent
+ * schedule (mc_run, mc_run_range, mc_nmpc_grad's closed loop; the paper has no
+ * counterpart: it describes where a launch's time goes).  Waits for that
+ * launch, then copies min(max_warps, W) records of MC_WARP_TRACE_WORDS uint64
+ * each into out_host (host memory) and writes the launch's warp count W to
+ * *n_warps_out.  Record w (warp = block w): [0] the pool rounds the warp ran,
+ * [1] its lane-rounds (the sum over those rounds of its lanes still holding a
+ * trajectory; over all warps, the launch's OCP starts plus line-search
+ * trials), [2] and [3] the GPU's global timer in ns when the warp started and
+ * finished, [4] the SM it ran on.  MC_ENOTRUN if no such launch has run on h;
+ * MC_EINVAL for a null h or n_warps_out, a negative max_warps, or a null
+ * out_host with max_warps > 0. */
+#define MC_WARP_TRACE_WORDS 5
+mc_status mc_copy_warp_trace(mc_handle* h, uint64_t* out_host, int64_t max_warps,
+                             int64_t* n_warps_out);
+
 /* Block until all work of the handle's last run has finished (timeout as in
  * mc_stats). */
 mc_status mc_sync(mc_handle* h, int64_t timeout_ms);
@@ -277,7 +293,14 @@ mc_status mc_set_nmpc_weights(mc_handle* h, double Qz, double Ru, double Qn);
  * Writes Phi_j, the counters (counter 7 also counts OCPs whose reduced
  * Hessian was not positive definite; their input tangent is 0) and
  * dPhi_j/d(Q_z, R_u, Q_n) per trajectory (read with mc_grad_mean,
- * mc_copy_grad).  Runs on the static schedule whatever the handle's.
+ * mc_copy_grad).  Runs on the handle's schedule, with the same results bit
+ * for bit: the static one carries the tangents along the closed loop; the
+ * persistent one records each sample's starting state and KKT point while it
+ * runs the closed loop, then propagates the tangents through the records with
+ * every lane of a warp on the same sample (records of at most 8 GB, chunks of
+ * trajectories beyond that).  Allocates on its first call 3 doubles per
+ * trajectory, 27 per scratch column and, on the persistent schedule, the
+ * records ((n_steps + 1) (5 (N + 1) + 8) doubles per trajectory of a chunk).
  * MC_EINVAL for a PI, mixed-precision or
  * three-state handle or a bad range; MC_ENOMEM if the gradient buffers
  * cannot be had. */

@@ -48,23 +48,61 @@ __global__ void __launch_bounds__(32) k_nmpc(DevModel m, DevCtrl c, int64_t j0, 
 }
 
 // The NMPC closed loop with the tangents of Phi_j in the weights (Q_z, R_u,
-// Q_n) (FP64, static schedule); dphi is n_sims x 3.
+// Q_n) (FP64, static schedule); dphi is n_sims x 3, tg kTgRows rows of ld
+// columns (the tangents in flight).
 __global__ void __launch_bounds__(32) k_nmpc_grad(DevModel m, DevCtrl c, int64_t j0, int64_t j1,
                                                   double* __restrict__ phi,
                                                   int32_t* __restrict__ cnt,
                                                   double* __restrict__ dphi, double* ws,
-                                                  int64_t ld) {
+                                                  int64_t ld, double* tg) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ld) return;
   const Ws w{ws + t, ld, c.N + 1};
+  const Tg g{tg + t, ld};
   for (int64_t j = j0 + t; j < j1; j += ld) {
-    double g[3];
     const TrajOut o = traj_nmpc_grad(m, c, (uint32_t)j, w, g);
     phi[j] = o.phi;
 #pragma unroll
     for (int q = 0; q < kNCounters; ++q) cnt[j * kNCounters + q] = o.cnt[q];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) dphi[j * 3 + q] = g[q];
+    grad_finish(m, o.phi, g, dphi + j * 3);
+  }
+}
+
+// The NMPC closed loop on the persistent schedule (FP64, launched as
+// k_nmpc_persist) that records, per sample, what the tangents of Phi_j need
+// (Recorder: trajectories rc.j0 .. rc.j0 + n - 1).
+__global__ void __launch_bounds__(32) k_nmpc_persist_rec(DevModel m, DevCtrl c, int64_t n,
+                                                         const uint32_t* order,
+                                                         unsigned long long* next,
+                                                         double* __restrict__ phi,
+                                                         int32_t* __restrict__ cnt, double* ws,
+                                                         int64_t ld, double* nz,
+                                                         unsigned long long* wtrace,
+                                                         Recorder rc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Ws w{ws + t, ld, c.N + 1};
+  nmpc_persistent<double, Recorder>(m, c, w, nz + t, rc.j0, n, order, next, phi, cnt, wtrace,
+                                    rc);
+}
+
+// The tangents of Phi_j through the recorded samples of trajectories
+// rc.j0 .. rc.j0 + n - 1, one thread per trajectory, ld threads (ld columns
+// of scratch and of tg, the tangents in flight); dphi is n_sims x 3.
+__global__ void __launch_bounds__(kTangentThreads) k_nmpc_tangent(DevModel m, DevCtrl c,
+                                                                  int64_t n,
+                                                                  const double* __restrict__ phi,
+                                                                  int32_t* __restrict__ cnt,
+                                                                  double* __restrict__ dphi,
+                                                                  double* ws, int64_t ld,
+                                                                  double* tg, Recorder rc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ld) return;
+  const Ws w{ws + t, ld, c.N + 1};
+  const Tg g{tg + t, ld};
+  for (int64_t q = t; q < n; q += ld) {
+    const int64_t j = rc.j0 + q;
+    traj_nmpc_tangent(m, c, (uint32_t)j, w, g, rc, phi[j], cnt + j * kNCounters + 7,
+                      dphi + j * 3);
   }
 }
 
@@ -103,13 +141,14 @@ __global__ void __launch_bounds__(32) k_nmpc_persist(DevModel m, DevCtrl c, int6
                                                      unsigned long long* next,
                                                      double* __restrict__ phi,
                                                      int32_t* __restrict__ cnt, double* ws,
-                                                     int64_t ld, double* nz) {
+                                                     int64_t ld, double* nz,
+                                                     unsigned long long* wtrace) {
   // launched with whole warps and at most ld threads; every lane takes part in
   // the warp votes of nmpc_persistent.  nz: 3 n_em rows of ld columns, the
-  // pooled plant noise.
+  // pooled plant noise; wtrace: the per-warp record (may be null).
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Ws w{ws + t, ld, c.N + 1};
-  nmpc_persistent<R>(m, c, w, nz + t, j0, n, order, next, phi, cnt);
+  nmpc_persistent<R>(m, c, w, nz + t, j0, n, order, next, phi, cnt, wtrace);
 }
 
 template <class R>
@@ -462,6 +501,9 @@ thread_local std::string g_create_error;
 // the 152 SMs as evenly as the warp granularity allows.
 constexpr int kNmpcThreads = 32;
 constexpr int kMaxStatBlocks = 1024;
+// Device memory the persistent NMPC gradient's sample records may take: 6.3 GB
+// hold the 30,000-trajectory, 240-step, N = 20 study in one chunk.
+constexpr size_t kRecordBudget = (size_t)8 << 30;
 
 struct DevBuf {
   void* p = nullptr;
@@ -501,6 +543,13 @@ struct mc_handle {
   double* ck = nullptr;        // checkpoints, 4 x n_ck x n_sims
   int64_t ck_words = 0;
   double* gmean = nullptr;     // mean gradient and the finite count
+  double* tg = nullptr;        // NMPC tangents in flight, kTgRows x ws_ld
+  double* rec = nullptr;       // the persistent NMPC gradient's sample records
+  size_t rec_bytes = 0;
+  int32_t* kj = nullptr;       // the sample each recorded trajectory ended at
+  // per-warp record of the last one-state persistent launch (ws_ld / 32 warps)
+  unsigned long long* wtrace = nullptr;
+  int64_t wtrace_warps = 0;
   bool grad_ran = false;
   // SM partition (green context): launches go to pstream, forked from and
   // joined back into the caller's stream
@@ -704,6 +753,10 @@ void mc_destroy(mc_handle* h) {
   cudaFree(h->dphi);
   cudaFree(h->ck);
   cudaFree(h->gmean);
+  cudaFree(h->tg);
+  cudaFree(h->rec);
+  cudaFree(h->kj);
+  cudaFree(h->wtrace);
   drop_partition(h);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -740,7 +793,9 @@ mc_status mc_create(const mc_model_t* model, const mc_controller_t* ctrl, int64_
     const size_t words =
         main_words + (h->c.nx_model == 3 ? 0 : (size_t)3 * h->m.n_em * (size_t)h->ws_ld);
     ok = alloc((void**)&h->ws, words * sizeof(double)) &&
-         alloc((void**)&h->next, sizeof(unsigned long long));
+         alloc((void**)&h->next, sizeof(unsigned long long)) &&
+         alloc((void**)&h->wtrace, sizeof(unsigned long long) * kWarpTraceWords *
+                                       (size_t)((h->ws_ld + kNmpcThreads - 1) / kNmpcThreads));
     if (ok) h->nz = h->ws + main_words;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -828,10 +883,11 @@ static mc_status enqueue_run(mc_handle* h, const DevModel& m, int64_t j0, int64_
                                                          h->cnt, h->ws, h->ws_ld);
       else if (h->c.precision == MC_FP64)
         k_nmpc_persist<double><<<blocks, kNmpcThreads, 0, st>>>(
-            m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz);
+            m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz, h->wtrace);
       else
         k_nmpc_persist<float><<<blocks, kNmpcThreads, 0, st>>>(
-            m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz);
+            m, h->c, j0, n, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz, h->wtrace);
+      if (h->c.nx_model != 3) h->wtrace_warps = blocks;
     } else if (h->c.kind == MC_CTRL_NMPC) {
       const int64_t n = j1 - j0;
       int64_t threads = n < h->ws_ld ? n : h->ws_ld;
@@ -1163,6 +1219,22 @@ mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
   return MC_OK;
 }
 
+mc_status mc_copy_warp_trace(mc_handle* h, uint64_t* out_host, int64_t max_warps,
+                             int64_t* n_warps_out) {
+  if (!h || !n_warps_out || max_warps < 0 || (max_warps > 0 && !out_host)) return MC_EINVAL;
+  *n_warps_out = 0;
+  if (h->wtrace_warps == 0)
+    return fail(h, MC_ENOTRUN, "no one-state persistent NMPC launch has run on this handle");
+  mc_status s = mc_sync(h, 0);
+  if (s != MC_OK) return s;
+  const int64_t n = h->wtrace_warps < max_warps ? h->wtrace_warps : max_warps;
+  if (n > 0)
+    MC_CUDA(h, cudaMemcpy(out_host, h->wtrace, sizeof(uint64_t) * kWarpTraceWords * n,
+                          cudaMemcpyDeviceToHost));
+  *n_warps_out = h->wtrace_warps;
+  return MC_OK;
+}
+
 // ------------------------------------------------ gradients of the PI study
 
 mc_status mc_set_pi_gains(mc_handle* h, double kP, double kI, double kaw) {
@@ -1258,15 +1330,62 @@ mc_status mc_nmpc_grad(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) 
       return fail(h, MC_ENOMEM, "cudaMalloc failed for the gradient buffers");
     }
   }
+  if (!h->tg && h->ws_ld > 0) {
+    if (cudaMalloc((void**)&h->tg, sizeof(double) * kTgRows * (size_t)h->ws_ld) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MC_ENOMEM, "cudaMalloc failed for the gradient buffers");
+    }
+  }
+  const int N1 = h->c.N + 1, RW = 5 * N1 + 8;
+  const size_t per_traj = sizeof(double) * (size_t)RW * (size_t)(h->m.n_steps + 1);
+  int64_t cn = (int64_t)(kRecordBudget / per_traj);
+  if (h->schedule == MC_SCHED_PERSISTENT && j1 > j0) {
+    // records of chunks of at most cn trajectories, allocated once per handle
+    cn = cn < 1 ? 1 : (cn > j1 - j0 ? j1 - j0 : cn);
+    if (h->rec_bytes < per_traj * (size_t)cn) {
+      cudaFree(h->rec);
+      h->rec = nullptr;
+      h->rec_bytes = 0;
+      if (cudaMalloc((void**)&h->rec, per_traj * (size_t)cn) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MC_ENOMEM, "cudaMalloc failed for the gradient's sample records");
+      }
+      h->rec_bytes = per_traj * (size_t)cn;
+    }
+    if (!h->kj && cudaMalloc((void**)&h->kj, sizeof(int32_t) * (size_t)h->n_sims) !=
+                      cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MC_ENOMEM, "cudaMalloc failed for the gradient's sample records");
+    }
+  }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   MC_CUDA(h, cudaEventRecord(h->ev0, st));
   const cudaStream_t ls = fork_stream(h, st);
-  if (j1 > j0) {
+  if (j1 > j0 && h->schedule == MC_SCHED_PERSISTENT) {
+    // each chunk: the recording closed loop (launched as enqueue_run launches
+    // k_nmpc_persist), then the tangent pass over its records
+    for (int64_t a = j0; a < j1; a += cn) {
+      const int64_t b = (j1 - a < cn) ? j1 : a + cn, nc = b - a;
+      const Recorder rc{h->rec, nc, a, RW, h->kj + a};
+      int64_t threads = nc < h->persist_threads ? nc : h->persist_threads;
+      threads = (threads + kNmpcThreads - 1) / kNmpcThreads * kNmpcThreads;
+      if (threads > h->ws_ld) threads = h->ws_ld;
+      const uint32_t* order = (a == 0 && b == h->n_sims) ? h->order : nullptr;
+      MC_CUDA(h, cudaMemsetAsync(h->next, 0, sizeof(unsigned long long), ls));
+      k_nmpc_persist_rec<<<(unsigned)(threads / kNmpcThreads), kNmpcThreads, 0, ls>>>(
+          h->m, h->c, nc, order, h->next, h->phi, h->cnt, h->ws, h->ws_ld, h->nz, h->wtrace, rc);
+      h->wtrace_warps = threads / kNmpcThreads;
+      const int64_t tt = nc < h->ws_ld ? nc : h->ws_ld;
+      k_nmpc_tangent<<<(unsigned)((tt + kTangentThreads - 1) / kTangentThreads),
+                       kTangentThreads, 0, ls>>>(h->m, h->c, nc, h->phi, h->cnt, h->dphi, h->ws,
+                                                 tt, h->tg, rc);
+    }
+  } else if (j1 > j0) {
     const int64_t n = j1 - j0;
     const int64_t threads = n < h->ws_ld ? n : h->ws_ld;
     const int64_t blocks = (threads + kNmpcThreads - 1) / kNmpcThreads;
     k_nmpc_grad<<<(unsigned)blocks, kNmpcThreads, 0, ls>>>(h->m, h->c, j0, j1, h->phi, h->cnt,
-                                                           h->dphi, h->ws, h->ws_ld);
+                                                           h->dphi, h->ws, h->ws_ld, h->tg);
   }
   k_grad_mean<<<1, kGradThreads, 0, ls>>>(h->phi, h->dphi, j0, j1, h->gmean);
   const mc_status s = launch_stats(h, j0, j1, ls);

@@ -380,17 +380,42 @@ __device__ __forceinline__ void pool_noise(const DevModel& m, double* nzl, int64
 // -- then the warp shoots all of it in the pool, and each lane finishes its
 // evaluation.  A started OCP takes its first QP in the next round's check,
 // together with the other lanes' checks, rather than on its own.
+//
+// With G::kRecord (G = the NMPC-weight gradient's Recorder, FP64) the loop
+// also hands the recorder, per sample, the state the sample starts from and
+// the OCP's KKT point; the tangents are propagated afterwards, by all lanes in
+// step.  G = NoRecord runs the closed loop alone.
+//
+// wtrace (may be null) receives the warp's record, kWarpTraceWords words per
+// warp (warp = block): the pool rounds it ran, its lane-rounds (the sum over
+// those rounds of its lanes still holding a trajectory), the GPU's global
+// timer (ns) when it started and finished, and the SM it ran on.
 enum LanePhase : int { kNewTraj = 0, kSample = 1, kCheck = 2, kTrial = 3, kStart = 4, kDone = 5 };
 
-template <class R>
+struct NoRecord {
+  static constexpr bool kRecord = false;
+};
+
+constexpr int kWarpTraceWords = 5;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class R, class G = NoRecord>
 __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w, double* nzl,
                                 int64_t j0, int64_t n, const uint32_t* __restrict__ order,
                                 unsigned long long* next, double* __restrict__ phi_out,
-                                int32_t* __restrict__ cnt_out) {
+                                int32_t* __restrict__ cnt_out,
+                                unsigned long long* __restrict__ wtrace, G g = G{}) {
   __shared__ PoolTab tab;  // one per block: the kernel runs one warp per block
   NmpcTraj T;
   SqpState s;
   int phase = kNewTraj;
+  const unsigned long long t_start = global_ns();
+  unsigned long long rounds = 0, lane_rounds = 0;
   for (;;) {
     // cheap, divergent phases until this lane needs shooting
     while (phase != kTrial && phase != kStart && phase != kDone) {
@@ -405,6 +430,7 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
         phase = kSample;
       }
       if (phase == kSample) {
+        if constexpr (G::kRecord) g.sample(w, T);
         if (nmpc_sample<R>(m, c, w, T, s, false)) {
           phase = kStart;
         } else {
@@ -412,12 +438,14 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
 #pragma unroll
           for (int q = 0; q < kNCounters; ++q)
             cnt_out[(int64_t)T.j * kNCounters + q] = T.out.cnt[q];
+          if constexpr (G::kRecord) g.finish(T);
           phase = kNewTraj;
         }
         continue;
       }
       if (phase == kCheck) {
         if (sqp_check<R>(c, w, s)) {
+          if constexpr (G::kRecord) g.ocp(w, T);
           nmpc_apply<R>(m, c, w, T, s.info, nzl, w.ld);
           phase = kSample;
         } else {
@@ -425,7 +453,10 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
         }
       }
     }
-    if (!__ballot_sync(0xffffffffu, phase != kDone)) break;
+    const unsigned busy = __ballot_sync(0xffffffffu, phase != kDone);
+    if (!busy) break;
+    ++rounds;
+    lane_rounds += (unsigned)__popc(busy);
     pool_noise<R>(m, nzl, w.ld, phase == kStart, T.j, T.i, tab);
     int n_jobs = 0, mode = kPoolTrial;
     if (phase == kTrial) {
@@ -445,10 +476,21 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       if (r == 0) {
         phase = kCheck;
       } else if (r == 1) {
+        if constexpr (G::kRecord) g.ocp(w, T);
         nmpc_apply<R>(m, c, w, T, s.info, nzl, w.ld);
         phase = kSample;
       }
     }
+  }
+  if (wtrace && (threadIdx.x & 31) == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    unsigned long long* o = wtrace + (int64_t)blockIdx.x * kWarpTraceWords;
+    o[0] = rounds;
+    o[1] = lane_rounds;
+    o[2] = t_start;
+    o[3] = global_ns();
+    o[4] = smid;
   }
 }
 

@@ -123,6 +123,9 @@ def lib():
             L.mc_ocp_sens_batch.argtypes = ([C.POINTER(McModel), C.POINTER(McController),
                                               C.c_int64] + [_dp] * 9 + [_ip])
             L.mc_ocp_sens_batch.restype = C.c_int
+            L.mc_copy_warp_trace.argtypes = [H, C.POINTER(C.c_uint64), C.c_int64,
+                                             C.POINTER(C.c_int64)]
+            L.mc_copy_warp_trace.restype = C.c_int
             for f in ("mc_exp_batch", "mc_rcp_batch"):
                 getattr(L, f).argtypes = [_dp, C.c_int64, _dp]
                 getattr(L, f).restype = C.c_int
@@ -141,6 +144,9 @@ def lib():
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
+
+
+WARP_TRACE_WORDS = 5   # MC_WARP_TRACE_WORDS
 
 
 def _check(status, handle=None, ok=(MC_OK,)):
@@ -293,6 +299,20 @@ class MonteCarlo:
         a = np.empty((n, N_COUNTERS), dtype=np.int32)
         _check(lib().mc_copy_counters(self._h, j0, n, a.ctypes.data_as(C.c_void_p), 0), self._h)
         return {k: a[:, i].copy() for i, k in enumerate(COUNTER_NAMES)}
+
+    def warp_trace(self) -> dict:
+        """Per-warp record of the last one-state persistent NMPC launch
+        (mc_copy_warp_trace): pool rounds, lane-rounds, start and end on the
+        GPU's global timer (ns), and the SM, one entry per warp."""
+        nw = C.c_int64()
+        _check(lib().mc_copy_warp_trace(self._h, None, 0, C.byref(nw)), self._h)
+        a = np.zeros((max(nw.value, 1), WARP_TRACE_WORDS), dtype=np.uint64)
+        _check(lib().mc_copy_warp_trace(self._h, a.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                        nw.value, C.byref(nw)), self._h)
+        a = a[:nw.value]
+        return {"rounds": a[:, 0].astype(np.int64), "lane_rounds": a[:, 1].astype(np.int64),
+                "t_start_ns": a[:, 2].astype(np.int64), "t_end_ns": a[:, 3].astype(np.int64),
+                "sm": a[:, 4].astype(np.int64)}
 
     # -- gradients of the PI study
 

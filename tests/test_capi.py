@@ -134,3 +134,14 @@ def test_reduce_noalloc_binding_rejects_bad_arrays_without_a_launch():
         mc.reduce_noalloc(123456, cnt, 8)
     with pytest.raises(ValueError):
         mc.reduce_noalloc(phi, cnt, -1)
+
+
+def test_warp_trace_layout_and_null_arguments(L):
+    """The record width is the same in the header, the kernel and the binding,
+    and null arguments are rejected before anything touches the device."""
+    hdr = open(os.path.join(ROOT, "include", "mc.h")).read()
+    assert int(re.search(r"#define MC_WARP_TRACE_WORDS (\d+)", hdr).group(1)) == mc.WARP_TRACE_WORDS
+    src = open(os.path.join(ROOT, "paper_2212_02197_gb300", "csrc", "mc_closedloop.cuh")).read()
+    assert int(re.search(r"kWarpTraceWords = (\d+)", src).group(1)) == mc.WARP_TRACE_WORDS
+    nw = C.c_int64(7)
+    assert L.mc_copy_warp_trace(None, None, 0, C.byref(nw)) == mc.MC_EINVAL

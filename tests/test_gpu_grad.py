@@ -218,12 +218,13 @@ def test_nmpc_grad_matches_oracle_per_trajectory():
 
 def test_nmpc_grad_full_study_sampled():
     """The NMPC-weight gradient of the full 30,000-trajectory, 240-step study
-    (R_u = 0.2, Q_n = 1) in one launch, as the benchmark times it; 24
-    trajectories across the index range against the oracle's complex-step
-    derivative, with the per-trajectory tolerances of the 40-step test."""
+    (R_u = 0.2, Q_n = 1) on the persistent schedule, as the benchmark times
+    it; 24 trajectories across the index range against the oracle's
+    complex-step derivative, with the per-trajectory tolerances of the
+    40-step test."""
     w = W.get(WL)
     n = w["n_traj"]
-    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="static")
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0, schedule="persistent")
     h = mc.MonteCarlo(w["model"], c, n, w["seed"])
     h.nmpc_grad()
     st = h.stats(timeout_ms=1800000)
@@ -257,6 +258,40 @@ def test_nmpc_grad_phi_equals_the_static_run():
     h.sync()
     assert np.array_equal(h.phi(), phi)
     h.close()
+
+
+@pytest.mark.parametrize("horizons", ["fixed", "mixed"])
+def test_nmpc_grad_persistent_is_bit_identical_to_static(horizons):
+    """The persistent schedule records each sample's starting state and KKT
+    point while it runs the closed loop, then propagates the tangents through
+    the records; per trajectory the arithmetic is the static schedule's, so
+    Phi, the tangents and the counters agree bit for bit (also with horizons
+    and iteration limits that differ between trajectories, and with the
+    records split into chunks)."""
+    w = W.get(WN)
+    m = dict(w["model"], n_steps=40)
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0)
+    if horizons == "mixed":
+        c.update(N_min=5, sqp_max_it_min=3)
+    n = 300
+    out = {}
+    for sched in ("static", "persistent"):
+        h = mc.MonteCarlo(m, dict(c, schedule=sched), n, w["seed"])
+        h.nmpc_grad()
+        h.sync()
+        out[sched] = (h.phi(), h.grad(), h.counters())
+        if sched == "persistent":   # a sub-range: the records of a chunk start at j0
+            h.nmpc_grad(j0=37, j1=250)
+            h.sync()
+            out["range"] = (h.phi()[37:250], h.grad()[37:250])
+        h.close()
+    (p0, g0, c0), (p1, g1, c1) = out["static"], out["persistent"]
+    assert np.array_equal(p0, p1)
+    assert np.array_equal(g0, g1)
+    for k in c0:
+        assert np.array_equal(c0[k], c1[k]), k
+    assert np.array_equal(out["range"][0], p0[37:250])
+    assert np.array_equal(out["range"][1], g0[37:250])
 
 
 def test_nmpc_gradient_matches_central_differences():

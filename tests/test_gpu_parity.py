@@ -541,6 +541,42 @@ def test_persistent_schedule_is_bit_identical_to_static(precision):
             assert np.array_equal(cnt[k], ref_cnt[k]), (key, k)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_warp_trace_accounts_for_every_round(precision):
+    """The per-warp record of a persistent launch: at every pool round a lane
+    that still holds a trajectory has exactly one OCP start or line-search
+    trial pending, so the lane-rounds of all warps add up to the launch's OCP
+    starts plus trials; each warp ran at least as many rounds as any of its
+    lanes' lane-rounds allow, and within the launch's time.  A static launch
+    leaves no record."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=40)
+    c = dict(w["nmpc"], precision=precision, schedule="persistent")
+    if precision == "mixed":
+        c.update(sqp_tol=1e-3, ls_max=3)
+    n = 200
+    h = mc.MonteCarlo(m, c, n, w["seed"])
+    h.run()
+    st = h.stats()
+    tr = h.warp_trace()
+    h.close()
+    assert len(tr["rounds"]) == (n + 31) // 32
+    assert tr["lane_rounds"].sum() == st["n_ocp"] + st["ls_trials"]
+    assert np.all(tr["lane_rounds"] <= 32 * tr["rounds"])
+    assert np.all(tr["rounds"] >= 1) and np.all(tr["t_end_ns"] >= tr["t_start_ns"])
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert np.all((tr["sm"] >= 0) & (tr["sm"] < sms))
+    hs = mc.MonteCarlo(m, dict(c, schedule="static"), 32, w["seed"])
+    hs.run()
+    hs.sync()
+    with pytest.raises(mc.McError) as e:
+        hs.warp_trace()
+    assert e.value.status == mc.MC_ENOTRUN
+    hs.close()
+
+
 def test_uneven_batch_matches_oracle():
     """Per-trajectory horizons 10..40 and SQP limits 5..30 (persistent
     schedule, queue ordered by horizon) against the oracle."""
