@@ -130,7 +130,7 @@ def nmpc_algorithmic_flops(cfg_model, cfg_ctrl, n_traj, st, w, opc):
     return flops
 
 
-def warp_trace_summary(h):
+def warp_trace_summary(h, n_steps=None):
     """Where the last persistent launch's time went, from its per-warp record
     (mc_copy_warp_trace): the SMs' busy share of the launch (last warp end
     minus first warp start on each SM, over the launch's span), the warps'
@@ -144,15 +144,27 @@ def warp_trace_summary(h):
     r = tr["rounds"].astype(float)
     dur = (t1 - t0).astype(float)
     slow = int(np.argmax(t1))
-    return {"warps": int(len(r)), "sms": int(len(busy)), "span_ms": span / 1e6,
-            "sm_busy_frac": float(np.mean(busy) / span),
-            "rounds_mean": float(r.mean()), "rounds_max": int(r.max()),
-            "lanes_per_round": float(tr["lane_rounds"].sum() / r.sum()),
-            "warp_ms_mean": float(dur.mean() / 1e6), "warp_ms_max": float(dur.max() / 1e6),
-            "last_warp": {"rounds": int(r[slow]), "ms": float(dur[slow] / 1e6),
-                          "us_per_round": float(dur[slow] / r[slow] / 1e3)},
-            "us_per_round_mean": float(np.mean(dur / r) / 1e3),
-            "corr_rounds_ms": float(np.corrcoef(r, dur)[0, 1])}
+    out = {"warps": int(len(r)), "sms": int(len(busy)), "span_ms": span / 1e6,
+           "sm_busy_frac": float(np.mean(busy) / span),
+           "rounds_mean": float(r.mean()), "rounds_max": int(r.max()),
+           "lanes_per_round": float(tr["lane_rounds"].sum() / r.sum()),
+           "warp_ms_mean": float(dur.mean() / 1e6), "warp_ms_max": float(dur.max() / 1e6),
+           "last_warp": {"rounds": int(r[slow]), "ms": float(dur[slow] / 1e6),
+                         "us_per_round": float(dur[slow] / r[slow] / 1e3)},
+           "us_per_round_mean": float(np.mean(dur / r) / 1e3),
+           "corr_rounds_ms": float(np.corrcoef(r, dur)[0, 1])}
+    if n_steps is not None:
+        # a trajectory's own rounds: one per OCP start and one per line-search
+        # trial; the warp's rounds are at least its slowest lane's
+        cnt = h.counters()
+        tr_r = n_steps + cnt["ls_trials"].astype(np.int64)
+        jm = int(np.argmax(tr_r))
+        out["trajectory_rounds"] = {
+            "mean": float(tr_r.mean()), "max": int(tr_r[jm]),
+            "slowest": {"j": jm, "ocps_at_iteration_limit": int(cnt["n_ocp_failed"][jm]),
+                        "sqp_iters": int(cnt["sqp_iters"][jm])},
+            "trajectories_with_an_ocp_at_the_limit": int((cnt["n_ocp_failed"] > 0).sum())}
+    return out
 
 
 def measured_peaks():
@@ -447,7 +459,7 @@ def main():
         roofline["achieved"], roofline["frac"] = pipe_tf, pipe_tf / peak
         roofline["work"] = roofline["pipe"]["work"]
     if w["nmpc"].get("schedule") == "persistent" and w["nmpc"].get("nx_model", 1) != 3:
-        roofline["warp_trace"] = warp_trace_summary(h_n)
+        roofline["warp_trace"] = warp_trace_summary(h_n, w["model"]["n_steps"])
 
     def timed(handles, n, label_ranges=True):
         """Mean device ms of n timed runs of the handles (in order, one stream),

@@ -501,7 +501,7 @@ thread_local std::string g_create_error;
 // the 152 SMs as evenly as the warp granularity allows.
 constexpr int kNmpcThreads = 32;
 constexpr int kMaxStatBlocks = 1024;
-// Device memory the persistent NMPC gradient's sample records may take: 6.3 GB
+// Device memory the persistent NMPC gradient's sample records may take: 6.5 GB
 // hold the 30,000-trajectory, 240-step, N = 20 study in one chunk.
 constexpr size_t kRecordBudget = (size_t)8 << 30;
 
