@@ -154,12 +154,13 @@ def warp_trace_summary(h, n_steps=None):
            "us_per_round_mean": float(np.mean(dur / r) / 1e3),
            "corr_rounds_ms": float(np.corrcoef(r, dur)[0, 1])}
     if n_steps is not None:
-        # a trajectory's own rounds: one per OCP start and one per line-search
-        # trial; the warp's rounds are at least its slowest lane's
+        # a trajectory's own trials: one per OCP start and one per line-search
+        # trial (a backtracking line search shoots several in one round, so
+        # this bounds the trajectory's rounds from above)
         cnt = h.counters()
         tr_r = n_steps + cnt["ls_trials"].astype(np.int64)
         jm = int(np.argmax(tr_r))
-        out["trajectory_rounds"] = {
+        out["trajectory_starts_and_trials"] = {
             "mean": float(tr_r.mean()), "max": int(tr_r[jm]),
             "slowest": {"j": jm, "ocps_at_iteration_limit": int(cnt["n_ocp_failed"][jm]),
                         "sqp_iters": int(cnt["sqp_iters"][jm])},

@@ -220,7 +220,8 @@ mc_status mc_copy_counters(mc_handle* h, int64_t j0, int64_t n, int32_t* dst,
  * *n_warps_out.  Record w (warp = block w): [0] the pool rounds the warp ran,
  * [1] its lane-rounds (the sum over those rounds of its lanes still holding a
  * trajectory; over all warps, the launch's OCP starts plus line-search
- * trials), [2] and [3] the GPU's global timer in ns when the warp started and
+ * rounds, where a backtracking line search tests several trials per round),
+ * [2] and [3] the GPU's global timer in ns when the warp started and
  * finished, [4] the SM it ran on.  MC_ENOTRUN if no such launch has run on h;
  * MC_EINVAL for a null h or n_warps_out, a negative max_warps, or a null
  * out_host with max_warps > 0. */

@@ -266,9 +266,10 @@ __device__ TrajOut traj_nmpc(const DevModel& m, const DevCtrl& c, uint32_t j, co
 
 enum PoolMode : int { kPoolTrial = 0, kPoolStartEnds = 1, kPoolStartAll = 2 };
 
+// A trial job's position is q N + k: interval k of line-search candidate q.
 struct PoolTab {
-  unsigned mask[MC_MAX_HORIZON];  // lanes with a job at position i
-  int pref[MC_MAX_HORIZON];       // jobs before position i
+  unsigned mask[MC_MAX_HORIZON * kLsCand];  // lanes with a job at position i
+  int pref[MC_MAX_HORIZON * kLsCand];       // jobs before position i
   double EaR[32];
   int N[32], mode[32];
   uint32_t j[32];                 // trajectory and sample of each lane's OCP
@@ -308,10 +309,12 @@ __device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, 
     for (int r = q - tab.pref[lo]; r > 0; --r) mo &= mo - 1u;
     const int o = __ffs(mo) - 1;
     const int md = tab.mode[o];
-    const int k = (md == kPoolStartEnds && lo == 1) ? tab.N[o] - 1 : lo;
     const bool trial = (md == kPoolTrial);
-    const int ua = trial ? UT : U, xa = trial ? XT : X;
-    const int aa = trial ? TA : EA, ba = trial ? TB : EB, ga = trial ? TG : EG;
+    const int cq = trial ? lo / tab.N[o] : 0;  // line-search candidate of a trial job
+    const int k = (md == kPoolStartEnds && lo == 1) ? tab.N[o] - 1 : lo - cq * tab.N[o];
+    const int ua = trial ? lsc_col(UT, cq) : U, xa = trial ? lsc_col(XT, cq) : X;
+    const int aa = trial ? lsc_col(TA, cq) : EA, ba = trial ? lsc_col(TB, cq) : EB;
+    const int ga = trial ? lsc_col(TG, cq) : EG;
     const Ws wo{w.p + (o - lane), w.ld, w.N1};
     const double xk = (k == 0) ? wo(X, 0) : wo(xa, k);
     const Shot r = shoot_interval<R>(m, c, tab.EaR[o], xk, wo(ua, k), wo(xa, k + 1), xs, ixs,
@@ -320,7 +323,7 @@ __device__ __forceinline__ void pool_shoot(const DevModel& m, const DevCtrl& c, 
     wo(ba, k) = r.B;
     wo(ga, k) = r.g;
     if (k == 0) {
-      const int pa = trial ? TPR : EPR;
+      const int pa = trial ? lsc_col(TPR, cq) : EPR;
       wo(pa, 0) = r.xpr;
       wo(pa, 1) = r.Ppr;
     }
@@ -378,7 +381,8 @@ __device__ __forceinline__ void pool_noise(const DevModel& m, double* nzl, int64
 // A round: each lane runs its cheap phases until it needs shooting -- a trial
 // point (kTrial), or the first evaluation of the OCP it just started (kStart)
 // -- then the warp shoots all of it in the pool, and each lane finishes its
-// evaluation.  A started OCP takes its first QP in the next round's check,
+// evaluation.  A lane whose line search backtracks has the next halvings shot
+// together (sqp_trial_points_spec) and tests them in order.  A started OCP takes its first QP in the next round's check,
 // together with the other lanes' checks, rather than on its own.
 //
 // With G::kRecord (G = the NMPC-weight gradient's Recorder, FP64) the loop
@@ -460,7 +464,7 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
     pool_noise<R>(m, nzl, w.ld, phase == kStart, T.j, T.i, tab);
     int n_jobs = 0, mode = kPoolTrial;
     if (phase == kTrial) {
-      n_jobs = s.N;
+      n_jobs = s.N * s.nc;
     } else if (phase == kStart) {
       const bool ends = (T.i > 0);
       mode = ends ? kPoolStartEnds : kPoolStartAll;
@@ -471,14 +475,20 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
       sqp_start_eval<R>(m, c, T.tp.EaR_c, w, s);
       phase = kCheck;
     } else if (phase == kTrial) {
-      sqp_eval_trial_shot<R>(m, c, T.tp.EaR_c, w, s);
-      const int r = sqp_trial_result<R>(c, w, s);
+      // the shot candidates in order, as the sequential line search tries them
+      int r = 2;
+      for (int q = 0; q < s.nc && r == 2; ++q) {
+        sqp_eval_trial_shot<R>(m, c, T.tp.EaR_c, w, s, q);
+        r = sqp_trial_result<R>(c, w, s, q, false);
+      }
       if (r == 0) {
         phase = kCheck;
       } else if (r == 1) {
         if constexpr (G::kRecord) g.ocp(w, T);
         nmpc_apply<R>(m, c, w, T, s.info, nzl, w.ld);
         phase = kSample;
+      } else {
+        sqp_trial_points_spec(c, w, s);  // backtracking: the next halvings, speculatively
       }
     }
   }

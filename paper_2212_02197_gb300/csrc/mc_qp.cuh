@@ -23,6 +23,10 @@
 
 namespace mc {
 
+// Line-search candidates the persistent schedule may shoot in one round when
+// it backtracks (candidate 0 is the trial point itself).
+constexpr int kLsCand = 4;
+
 enum Arr : int {
   U, X, LAM, PIL, PIU,            // SQP iterate and warm start
   WXX, WXU, WUU,                  // block-BFGS Hessian blocks
@@ -37,8 +41,18 @@ enum Arr : int {
   VB,                             // steady-state inputs vbar_k of the set-points (R_u term)
   PIN, TPR, EPR,                  // P_{i|i} (row 0); the CD-EKF prediction (x, P in rows 0,
                                   // 1) carried by the interval-0 shooting: trial, current
-  kNArr
+  LSC,                            // line-search candidates 1 .. kLsCand-1: 7 columns each,
+                                  // as UT, XT, TA, TB, TG, TQ, TPR
+  kNArr = LSC + 7 * (kLsCand - 1)
 };
+
+// Column a (one of UT, XT, TA, TB, TG, TQ, TPR) of line-search candidate q.
+__host__ __device__ constexpr int lsc_col(int a, int q) {
+  return q == 0 ? a
+                : LSC + 7 * (q - 1) +
+                      (a == UT ? 0 : a == XT ? 1 : a == TA ? 2 : a == TB ? 3 : a == TG ? 4
+                                                  : a == TQ ? 5 : 6);
+}
 
 struct Ws {
   double* p;

@@ -31,6 +31,8 @@ struct SqpState {
   int N, max_it;      // horizon and iteration limit of this OCP
   int l;              // iteration counter
   int hv;             // halvings in the current line search
+  int nc;             // line-search candidates set up for the next evaluation (1
+                      // unless the persistent schedule backtracks speculatively)
   bool pt_ready;      // pt holds the trial point's penalty sigma^T |g|
   double f, ft, pt, alpha, T0, DT0;
   SqpInfo info;
@@ -237,6 +239,30 @@ __device__ __forceinline__ void sqp_trial_point(const DevCtrl& c, const Ws& w,
                    ws_col(w, X), ws_col(w, DX), ws_col(w, UT), ws_col(w, XT));
 }
 
+// Speculative backtracking (persistent schedule): after a failed trial, the
+// trial points of the next nc halvings, alpha, alpha/2, ..., alpha/2^(nc-1)
+// (exact: powers of two), each in its candidate's columns, so that the pool
+// shoots them in one round.  nc doubles with every round the line search
+// keeps failing (2, then kLsCand), and never passes the halving limit.  The
+// candidates are then tested in order with the same Armijo rule, so the
+// accepted step, the iterates and the trial count are those of the
+// sequential line search; the shot candidates after the accepted one are
+// the price.
+__device__ __forceinline__ void sqp_trial_points_spec(const DevCtrl& c, const Ws& w,
+                                                      SqpState& s) {
+  int nc = (s.hv <= 1) ? 2 : kLsCand;
+  const int left = c.ls_max - s.hv + 1;  // trials the halving limit still allows
+  nc = nc < left ? nc : left;
+  nc = nc < 1 ? 1 : nc;
+  double a = s.alpha;
+  for (int q = 0; q < nc; ++q) {
+    trial_point_pass(s.N, w.ld, a, c.vmin, c.vmax, ws_col(w, U), ws_col(w, DU), ws_col(w, X),
+                     ws_col(w, DX), ws_col(w, lsc_col(UT, q)), ws_col(w, lsc_col(XT, q)));
+    a *= 0.5;
+  }
+  s.nc = nc;
+}
+
 // Start an OCP from the warm start in (U, X, LAM, PIL, PIU) with x0 and the
 // set-points z-bar(t_{i+k}) in ZB[1..N]; W^[0] = I.  With shifted_eval the
 // evaluation arrays hold the previous OCP's final evaluation shifted by one
@@ -252,6 +278,7 @@ __device__ __forceinline__ void sqp_start(const DevModel& m, const DevCtrl& c, d
   s.max_it = max_it;
   s.l = 0;
   s.hv = 0;
+  s.nc = 1;
   s.pt_ready = false;
   s.alpha = 0.0;
   s.info = SqpInfo{};
@@ -457,6 +484,7 @@ __device__ __forceinline__ bool sqp_check_body(const DevCtrl& c, const Ws& w, Sq
   s.DT0 = dfd - pen;
   s.alpha = 1.0;
   s.hv = 0;
+  s.nc = 1;
   return false;
 }
 
@@ -487,16 +515,19 @@ __device__ __forceinline__ void trial_objective_pass(
 }
 
 // The same trial evaluation after the warp has shot the intervals (the
-// persistent schedule's pool): only the objective, q_k and the penalty.
+// persistent schedule's pool): only the objective, q_k and the penalty, of
+// line-search candidate q.
 template <class R>
 __device__ __forceinline__ void sqp_eval_trial_shot(const DevModel& m, const DevCtrl& c,
-                                                    double EaR, const Ws& w, SqpState& s) {
+                                                    double EaR, const Ws& w, SqpState& s,
+                                                    int q = 0) {
   const double xs = c.x_scale;
   const double qf = 2.0 * c.Qz * m.Ts * xs * m.iV;
   double f, pt;
-  trial_objective_pass(s.N, w.ld, c.Qz, m.Ts, xs, m.iV, qf, ws_col(w, XT), ws_col(w, ZB),
-                       ws_col(w, TQ), ws_col(w, SIG), ws_col(w, TG), f, pt);
-  s.ft = f + objective_extra(m, c, s.N, w, UT, XT, TQ);
+  trial_objective_pass(s.N, w.ld, c.Qz, m.Ts, xs, m.iV, qf, ws_col(w, lsc_col(XT, q)),
+                       ws_col(w, ZB), ws_col(w, lsc_col(TQ, q)), ws_col(w, SIG),
+                       ws_col(w, lsc_col(TG, q)), f, pt);
+  s.ft = f + objective_extra(m, c, s.N, w, lsc_col(UT, q), lsc_col(XT, q), lsc_col(TQ, q));
   s.pt = pt;
   s.pt_ready = true;
   s.info.ls_trials++;
@@ -552,12 +583,14 @@ __device__ __forceinline__ void accept_pass(
   }
 }
 
-// Armijo test of the evaluated trial point.  Returns 0 when the step was
-// accepted (xi^[l+1] is current and evaluated; continue with sqp_check),
-// 1 when the line search ran out of halvings (status 2; the OCP is finished
-// at the current iterate), 2 when the step was halved (evaluate the new trial).
+// Armijo test of the evaluated trial point (line-search candidate q).  Returns
+// 0 when the step was accepted (xi^[l+1] is current and evaluated; continue
+// with sqp_check), 1 when the line search ran out of halvings (status 2; the
+// OCP is finished at the current iterate), 2 when the step was halved
+// (evaluate the new trial; its trial point is set up here when next_point).
 __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws& w,
-                                                     SqpState& s) {
+                                                     SqpState& s, int q = 0,
+                                                     bool next_point = true) {
   const int N = s.N;
   const double c1 = 1e-4;
   double pt = 0.0;
@@ -573,17 +606,19 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
     }
     s.hv++;
     s.alpha *= 0.5;
-    sqp_trial_point(c, w, s);
+    if (next_point) sqp_trial_point(c, w, s);
     return 2;
   }
   const double alpha = s.alpha;
   accept_pass(N, w.ld, alpha, c.Ru != 0.0, ws_col(w, MU), ws_col(w, NUL), ws_col(w, NUU),
               ws_col(w, LAM), ws_col(w, PIL), ws_col(w, PIU), ws_col(w, QR), ws_col(w, GLU),
-              ws_col(w, GLX), ws_col(w, UT), ws_col(w, U), ws_col(w, DU), ws_col(w, XT),
-              ws_col(w, X), ws_col(w, TA), ws_col(w, EA), ws_col(w, TB), ws_col(w, EB),
-              ws_col(w, TG), ws_col(w, EG), ws_col(w, TQ), ws_col(w, EQ));
-  w(EPR, 0) = w(TPR, 0);
-  w(EPR, 1) = w(TPR, 1);
+              ws_col(w, GLX), ws_col(w, lsc_col(UT, q)), ws_col(w, U), ws_col(w, DU),
+              ws_col(w, lsc_col(XT, q)), ws_col(w, X), ws_col(w, lsc_col(TA, q)),
+              ws_col(w, EA), ws_col(w, lsc_col(TB, q)), ws_col(w, EB),
+              ws_col(w, lsc_col(TG, q)), ws_col(w, EG), ws_col(w, lsc_col(TQ, q)),
+              ws_col(w, EQ));
+  w(EPR, 0) = w(lsc_col(TPR, q), 0);
+  w(EPR, 1) = w(lsc_col(TPR, q), 1);
   s.f = s.ft;
   s.l++;
   return 0;
@@ -596,8 +631,9 @@ __device__ __forceinline__ int sqp_trial_result_body(const DevCtrl& c, const Ws&
 __device__ __noinline__ bool sqp_check_call(const DevCtrl& c, const Ws& w, SqpState& s) {
   return sqp_check_body(c, w, s);
 }
-__device__ __noinline__ int sqp_trial_result_call(const DevCtrl& c, const Ws& w, SqpState& s) {
-  return sqp_trial_result_body(c, w, s);
+__device__ __noinline__ int sqp_trial_result_call(const DevCtrl& c, const Ws& w, SqpState& s,
+                                                  int q, bool next_point) {
+  return sqp_trial_result_body(c, w, s, q, next_point);
 }
 template <class R>
 __device__ __forceinline__ bool sqp_check(const DevCtrl& c, const Ws& w, SqpState& s) {
@@ -605,9 +641,10 @@ __device__ __forceinline__ bool sqp_check(const DevCtrl& c, const Ws& w, SqpStat
   else return sqp_check_body(c, w, s);
 }
 template <class R>
-__device__ __forceinline__ int sqp_trial_result(const DevCtrl& c, const Ws& w, SqpState& s) {
-  if constexpr (sizeof(R) == 4) return sqp_trial_result_call(c, w, s);
-  else return sqp_trial_result_body(c, w, s);
+__device__ __forceinline__ int sqp_trial_result(const DevCtrl& c, const Ws& w, SqpState& s,
+                                                int q = 0, bool next_point = true) {
+  if constexpr (sizeof(R) == 4) return sqp_trial_result_call(c, w, s, q, next_point);
+  else return sqp_trial_result_body(c, w, s, q, next_point);
 }
 
 // SQP of Sec. IV for one OCP, all phases in sequence.  Returns diagnostics;

@@ -542,13 +542,41 @@ def test_persistent_schedule_is_bit_identical_to_static(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_speculative_backtracking_is_bit_identical_to_static(precision):
+    """The persistent schedule shoots the next halvings of a backtracking line
+    search together and tests them in order; the static schedule tries one
+    trial point at a time.  On the first 24 steps of the 100k study (N = 30,
+    E_a lognormal 2 %), where many SQP iterations sit at the merit's rounding
+    floor and backtrack, Phi and every counter (iterations, trials, iteration
+    limits, line-search failures) agree bit for bit."""
+    w = W.get("cstr_100k_x240_N30_mixed")
+    m = dict(w["model"], n_steps=24)
+    c = dict(w["nmpc"], precision="fp64", sqp_tol=1e-5, ls_max=30)
+    if precision == "mixed":
+        c.update(precision="mixed", sqp_tol=1e-3, ls_max=3)
+    n = 256
+    out = {}
+    for sched in ("static", "persistent"):
+        h = mc.MonteCarlo(m, dict(c, schedule=sched), n, w["seed"])
+        h.run()
+        st = h.stats()
+        out[sched] = (h.phi(), h.counters(), st)
+        h.close()
+    (p0, c0, s0), (p1, c1, s1) = out["static"], out["persistent"]
+    assert s0["ls_trials"] > 1.2 * s0["sqp_iters"], (s0["ls_trials"], s0["sqp_iters"])
+    assert np.array_equal(p0, p1)
+    for k in c0:
+        assert np.array_equal(c0[k], c1[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_warp_trace_accounts_for_every_round(precision):
     """The per-warp record of a persistent launch: at every pool round a lane
-    that still holds a trajectory has exactly one OCP start or line-search
-    trial pending, so the lane-rounds of all warps add up to the launch's OCP
-    starts plus trials; each warp ran at least as many rounds as any of its
-    lanes' lane-rounds allow, and within the launch's time.  A static launch
-    leaves no record."""
+    that still holds a trajectory has one OCP start or one line-search round
+    pending (a round of a backtracking line search shoots several trials), so
+    the lane-rounds of all warps lie between the launch's OCP starts plus SQP
+    iterations (one trial each at least) and its OCP starts plus trials; each
+    warp ran within the launch's time.  A static launch leaves no record."""
     w = W.get("cstr_100x120_N20_fp64")
     m = dict(w["model"], n_steps=40)
     c = dict(w["nmpc"], precision=precision, schedule="persistent")
@@ -561,7 +589,8 @@ def test_warp_trace_accounts_for_every_round(precision):
     tr = h.warp_trace()
     h.close()
     assert len(tr["rounds"]) == (n + 31) // 32
-    assert tr["lane_rounds"].sum() == st["n_ocp"] + st["ls_trials"]
+    lr = tr["lane_rounds"].sum()
+    assert st["n_ocp"] + st["sqp_iters"] <= lr <= st["n_ocp"] + st["ls_trials"]
     assert np.all(tr["lane_rounds"] <= 32 * tr["rounds"])
     assert np.all(tr["rounds"] >= 1) and np.all(tr["t_end_ns"] >= tr["t_start_ns"])
     import torch
