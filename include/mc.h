@@ -126,6 +126,11 @@ typedef struct {
    * set-point zbar_k; one-state model only                                  */
   double Ru;
   double Qn;
+  /* persistent schedule: a backtracking line search shoots its next halvings
+   * together (speculative backtracking; the same iterates and counters as
+   * one trial at a time) while at most this many lanes of its warp hold a
+   * trajectory; 0 = always, negative = never, 1..32 = that many lanes    */
+  int32_t ls_spec_lanes;
 } mc_controller_t;
 
 typedef enum {

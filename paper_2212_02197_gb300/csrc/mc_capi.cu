@@ -619,6 +619,7 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
       return bad("unknown schedule");
     if (cc->threads_per_sm < 0 || cc->threads_per_sm > 2048)
       return bad("threads_per_sm must be 0..2048");
+    if (cc->ls_spec_lanes > 32) return bad("ls_spec_lanes must be <= 32");
     if (cc->nx_model != 0 && cc->nx_model != 1 && cc->nx_model != 3)
       return bad("nx_model must be 0, 1 or 3");
     if (!(cc->Ru >= 0.0) || !(cc->Qn >= 0.0) || !std::isfinite(cc->Ru) || !std::isfinite(cc->Qn))
@@ -673,6 +674,7 @@ static mc_status fill_dev(const mc_model_t* mm, const mc_controller_t* cc, uint6
   memset(c, 0, sizeof(*c));
   c->kind = cc->kind; c->precision = cc->precision; c->N = cc->N; c->n_rk4 = cc->n_rk4;
   c->sqp_max_it = cc->sqp_max_it; c->ls_max = cc->ls_max; c->qp_solver = cc->qp_solver;
+  c->spec_lanes = cc->ls_spec_lanes == 0 ? 32 : (cc->ls_spec_lanes < 0 ? 0 : cc->ls_spec_lanes);
   c->ip_max_it = cc->ip_max_it;
   c->u_min = cc->u_min; c->u_max = cc->u_max; c->kP = cc->kP; c->kI = cc->kI; c->kaw = cc->kaw;
   c->Qz = cc->Qz; c->P0 = cc->P0; c->sqp_tol = cc->sqp_tol; c->ip_tol = cc->ip_tol;

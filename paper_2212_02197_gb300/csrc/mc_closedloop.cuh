@@ -459,8 +459,9 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
     }
     const unsigned busy = __ballot_sync(0xffffffffu, phase != kDone);
     if (!busy) break;
+    const int nbusy = __popc(busy);
     ++rounds;
-    lane_rounds += (unsigned)__popc(busy);
+    lane_rounds += (unsigned)nbusy;
     pool_noise<R>(m, nzl, w.ld, phase == kStart, T.j, T.i, tab);
     int n_jobs = 0, mode = kPoolTrial;
     if (phase == kTrial) {
@@ -488,7 +489,7 @@ __device__ void nmpc_persistent(const DevModel& m, const DevCtrl& c, const Ws& w
         nmpc_apply<R>(m, c, w, T, s.info, nzl, w.ld);
         phase = kSample;
       } else {
-        sqp_trial_points_spec(c, w, s);  // backtracking: the next halvings, speculatively
+        sqp_trial_points_spec(c, w, s, nbusy);  // backtracking: the next halvings together
       }
     }
   }

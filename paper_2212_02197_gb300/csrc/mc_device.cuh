@@ -44,6 +44,7 @@ struct DevCtrl {
   int sqp_max_it, ls_max, qp_solver, ip_max_it;
   int N_min, it_min;   // > 0: per-trajectory N in [N_min, N], limit in [it_min, sqp_max_it]
   int nx_model;        // NMPC model: 1 = one-state, 3 = three-state
+  int spec_lanes;      // speculative backtracking while at most this many lanes are busy
   double Ru, Qn;       // input-deviation and terminal weights of the extended objective
   double r_scale;      // 2 R_u T_s: r_k = r_scale (v_k - vbar_{k+1})
   double u_min, u_max, kP, kI, kaw, Qz, P0, sqp_tol, ip_tol, u_scale, x_scale;

@@ -247,10 +247,11 @@ __device__ __forceinline__ void sqp_trial_point(const DevCtrl& c, const Ws& w,
 // candidates are then tested in order with the same Armijo rule, so the
 // accepted step, the iterates and the trial count are those of the
 // sequential line search; the shot candidates after the accepted one are
-// the price.
+// the price, which only pays while the warp has idle lanes: with more than
+// c.spec_lanes of its lanes busy (nbusy) there is one trial point.
 __device__ __forceinline__ void sqp_trial_points_spec(const DevCtrl& c, const Ws& w,
-                                                      SqpState& s) {
-  int nc = (s.hv <= 1) ? 2 : kLsCand;
+                                                      SqpState& s, int nbusy) {
+  int nc = (nbusy > c.spec_lanes) ? 1 : (s.hv <= 1) ? 2 : kLsCand;
   const int left = c.ls_max - s.hv + 1;  // trials the halving limit still allows
   nc = nc < left ? nc : left;
   nc = nc < 1 ? 1 : nc;

@@ -53,7 +53,8 @@ class McController(C.Structure):
                 ("ip_max_it", C.c_int32), ("ip_tol", C.c_double), ("u_scale", C.c_double),
                 ("x_scale", C.c_double), ("N_min", C.c_int32), ("sqp_max_it_min", C.c_int32),
                 ("schedule", C.c_int32), ("threads_per_sm", C.c_int32),
-                ("nx_model", C.c_int32), ("Ru", C.c_double), ("Qn", C.c_double)]
+                ("nx_model", C.c_int32), ("Ru", C.c_double), ("Qn", C.c_double),
+                ("ls_spec_lanes", C.c_int32)]
 
 
 class McStats(C.Structure):
@@ -195,6 +196,7 @@ def make_ctrl(cd: dict) -> McController:
     c.sqp_max_it_min = int(cd.get("sqp_max_it_min", 0))
     c.schedule = SCHEDULES[cd.get("schedule", "static")]
     c.threads_per_sm = int(cd.get("threads_per_sm", 0))
+    c.ls_spec_lanes = int(cd.get("ls_spec_lanes", 0))
     c.nx_model = int(cd.get("nx_model", 1))
     c.Ru = float(cd.get("Ru", 0.0))
     c.Qn = float(cd.get("Qn", 0.0))

@@ -67,6 +67,7 @@ def _bad(model=None, ctrl=None, n=10):
     ({"sp_time": [0.0, 10.0, 5.0], "sp_value": [1.0, 2.0, 3.0]}, {}, "increase"),
     ({}, {"sqp_tol": 0.0}, "sqp_tol"),
     ({}, {"qp_solver": "ipm", "ip_max_it": 0}, "interior-point"),
+    ({}, {"ls_spec_lanes": 33}, "ls_spec_lanes"),
 ])
 def test_invalid_configurations_are_rejected(L, model, ctrl, needle):
     assert needle in _bad(model, ctrl)

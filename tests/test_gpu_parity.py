@@ -541,8 +541,8 @@ def test_persistent_schedule_is_bit_identical_to_static(precision):
             assert np.array_equal(cnt[k], ref_cnt[k]), (key, k)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_speculative_backtracking_is_bit_identical_to_static(precision):
+@pytest.mark.parametrize("precision,spec_lanes", [("fp64", 0), ("fp64", 8), ("mixed", 0)])
+def test_speculative_backtracking_is_bit_identical_to_static(precision, spec_lanes):
     """The persistent schedule shoots the next halvings of a backtracking line
     search together and tests them in order; the static schedule tries one
     trial point at a time.  On the first 24 steps of the 100k study (N = 30,
@@ -557,7 +557,7 @@ def test_speculative_backtracking_is_bit_identical_to_static(precision):
     n = 256
     out = {}
     for sched in ("static", "persistent"):
-        h = mc.MonteCarlo(m, dict(c, schedule=sched), n, w["seed"])
+        h = mc.MonteCarlo(m, dict(c, schedule=sched, ls_spec_lanes=spec_lanes), n, w["seed"])
         h.run()
         st = h.stats()
         out[sched] = (h.phi(), h.counters(), st)
