@@ -79,10 +79,10 @@ OPCOUNTS = os.path.join(ROOT, "oracle", "opcounts.json")
 
 # DRAM bytes (read + write) of k_nmpc_persist<double> per control step of the
 # 30,000-trajectory FP64 study, from one ncu capture of a 60-step case of it
-# (dram__bytes_read.sum 62.50 GB + dram__bytes_write.sum 78.70 GB).  A full
+# (dram__bytes_read.sum 59.48 GB + dram__bytes_write.sum 76.15 GB).  A full
 # launch is scaled by its steps and trajectories.
 TRAFFIC_WORKLOAD = "cstr_30k_x240_N20_fp64"
-TRAFFIC_BYTES_PER_STEP_30K = (62495836160 + 78695064320) / 60
+TRAFFIC_BYTES_PER_STEP_30K = (59476805000 + 76153419000) / 60
 
 
 def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st, w):

@@ -288,6 +288,16 @@ mc_status mc_pi_grad(mc_handle* h, int64_t j0, int64_t j1, int32_t checkpoint_ev
  * three-state model. */
 mc_status mc_set_nmpc_weights(mc_handle* h, double Qz, double Ru, double Qn);
 
+/* Device memory the persistent schedule's mc_nmpc_grad may take for its
+ * sample records (the paper has no counterpart): bytes >= the records of one
+ * trajectory, (n_steps + 1) (5 (N + 1) + 8) doubles; 0 restores the default
+ * of 8 GB.  Smaller budgets split the trajectories into more chunks, each a
+ * recording launch and a tangent launch; the results do not change.  Takes
+ * effect at the next mc_nmpc_grad, which reallocates the records only when
+ * they must grow.  MC_EINVAL for a null or non-NMPC handle, a negative
+ * budget, or one below a trajectory's records. */
+mc_status mc_set_grad_record_budget(mc_handle* h, int64_t bytes);
+
 /* Run trajectories j0 .. j1-1 of an NMPC handle (one-state model, FP64) and
  * the tangents of Phi_j with respect to the weights (Q_z, R_u, Q_n) of the
  * extended objective (mc_controller_t.Ru, .Qn; the paper's has both 0), on

@@ -546,6 +546,7 @@ struct mc_handle {
   double* tg = nullptr;        // NMPC tangents in flight, kTgRows x ws_ld
   double* rec = nullptr;       // the persistent NMPC gradient's sample records
   size_t rec_bytes = 0;
+  size_t rec_budget = kRecordBudget;  // bytes the records may take
   int32_t* kj = nullptr;       // the sample each recorded trajectory ended at
   // per-warp record of the last one-state persistent launch (ws_ld / 32 warps)
   unsigned long long* wtrace = nullptr;
@@ -1318,6 +1319,18 @@ mc_status mc_set_nmpc_weights(mc_handle* h, double Qz, double Ru, double Qn) {
   return MC_OK;
 }
 
+mc_status mc_set_grad_record_budget(mc_handle* h, int64_t bytes) {
+  if (!h) return MC_EINVAL;
+  if (h->c.kind != MC_CTRL_NMPC)
+    return fail(h, MC_EINVAL, "mc_set_grad_record_budget needs an NMPC handle");
+  const size_t per_traj =
+      sizeof(double) * (size_t)(5 * (h->c.N + 1) + 8) * (size_t)(h->m.n_steps + 1);
+  if (bytes < 0 || (bytes > 0 && (size_t)bytes < per_traj))
+    return fail(h, MC_EINVAL, "the record budget must be 0 or hold one trajectory's records");
+  h->rec_budget = bytes == 0 ? kRecordBudget : (size_t)bytes;
+  return MC_OK;
+}
+
 mc_status mc_nmpc_grad(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) {
   if (!h) return MC_EINVAL;
   if (h->c.kind != MC_CTRL_NMPC) return fail(h, MC_EINVAL, "mc_nmpc_grad needs an NMPC handle");
@@ -1340,7 +1353,7 @@ mc_status mc_nmpc_grad(mc_handle* h, int64_t j0, int64_t j1, void* cuda_stream) 
   }
   const int N1 = h->c.N + 1, RW = 5 * N1 + 8;
   const size_t per_traj = sizeof(double) * (size_t)RW * (size_t)(h->m.n_steps + 1);
-  int64_t cn = (int64_t)(kRecordBudget / per_traj);
+  int64_t cn = (int64_t)(h->rec_budget / per_traj);
   if (h->schedule == MC_SCHED_PERSISTENT && j1 > j0) {
     // records of chunks of at most cn trajectories, allocated once per handle
     cn = cn < 1 ? 1 : (cn > j1 - j0 ? j1 - j0 : cn);

@@ -127,6 +127,8 @@ def lib():
             L.mc_copy_warp_trace.argtypes = [H, C.POINTER(C.c_uint64), C.c_int64,
                                              C.POINTER(C.c_int64)]
             L.mc_copy_warp_trace.restype = C.c_int
+            L.mc_set_grad_record_budget.argtypes = [H, C.c_int64]
+            L.mc_set_grad_record_budget.restype = C.c_int
             for f in ("mc_exp_batch", "mc_rcp_batch"):
                 getattr(L, f).argtypes = [_dp, C.c_int64, _dp]
                 getattr(L, f).restype = C.c_int
@@ -330,6 +332,10 @@ class MonteCarlo:
 
     def set_nmpc_weights(self, Qz: float, Ru: float, Qn: float):
         _check(lib().mc_set_nmpc_weights(self._h, float(Qz), float(Ru), float(Qn)), self._h)
+
+    def set_grad_record_budget(self, nbytes: int):
+        """Device memory the persistent gradient's sample records may take (0: 8 GB)."""
+        _check(lib().mc_set_grad_record_budget(self._h, int(nbytes)), self._h)
 
     def nmpc_grad(self, stream=None, j0: int = 0, j1: int | None = None):
         """Closed loop with the tangents of Phi in (Q_z, R_u, Q_n) (asynchronous)."""

@@ -294,6 +294,37 @@ def test_nmpc_grad_persistent_is_bit_identical_to_static(horizons):
     assert np.array_equal(out["range"][1], g0[37:250])
 
 
+def test_nmpc_grad_in_record_chunks_is_bit_identical():
+    """A record budget of a few trajectories' records splits the persistent
+    gradient into many chunks (each a recording launch and a tangent launch,
+    the chunks' records reusing one buffer); the results are those of one
+    chunk and of the static schedule, bit for bit.  A budget below one
+    trajectory's records is rejected."""
+    w = W.get(WN)
+    m = dict(w["model"], n_steps=30)
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0)
+    n = 200
+    per_traj = 8 * (5 * (c["N"] + 1) + 8) * (m["n_steps"] + 1)
+    out = {}
+    for key, sched, budget in (("static", "static", 0), ("one", "persistent", 0),
+                               ("chunks", "persistent", 23 * per_traj)):
+        h = mc.MonteCarlo(m, dict(c, schedule=sched), n, w["seed"])
+        h.set_grad_record_budget(budget)
+        h.nmpc_grad()
+        h.sync()
+        out[key] = (h.phi(), h.grad(), h.counters())
+        if key == "chunks":
+            with pytest.raises(mc.McError) as e:
+                h.set_grad_record_budget(per_traj - 8)
+            assert e.value.status == mc.MC_EINVAL
+        h.close()
+    for key in ("one", "chunks"):
+        assert np.array_equal(out[key][0], out["static"][0]), key
+        assert np.array_equal(out[key][1], out["static"][1]), key
+        for q in out["static"][2]:
+            assert np.array_equal(out[key][2][q], out["static"][2][q]), (key, q)
+
+
 def test_nmpc_gradient_matches_central_differences():
     """The tangent is the derivative of the closed loop whose OCPs sit exactly
     at their KKT points.  Phi_j is only piecewise smooth in the weights: where
