@@ -63,6 +63,18 @@ struct Ws {
   }
 };
 
+// 1/x for the recursions below: on the device the Newton-refined hardware
+// reciprocal (rcp_newton: four dependent operations on the pipe instead of a
+// division's longer sequence, on the Riccati recursion's critical path), on
+// the host the division.
+MC_HD double recip(double x) {
+#ifdef __CUDA_ARCH__
+  return rcp_newton(x);
+#else
+  return 1.0 / x;
+#endif
+}
+
 struct QpResult {
   int iters;
   int status;  // 0 solved, 1 iteration limit, 2 not positive definite
@@ -98,7 +110,7 @@ MC_HD bool riccati_backward(const Ws& w, int N, uint64_t fixed, RkF rk_of,
     } else {
       const double Rb = w(WUU, k) + extra_of(k) + B * B * P;
       if (!(Rb > 0.0)) return false;
-      const double iR = 1.0 / Rb;
+      const double iR = recip(Rb);
       const double Sb = (k > 0) ? w(WXU, k) + A * P * B : 0.0;
       const double sb = rk_of(k) + B * Pbp;
       w(RK, k) = -Sb * iR;
@@ -162,7 +174,7 @@ MC_HD bool as_backward(int N, int64_t ld, uint64_t fixed, bool has_r,
     } else {
       const double Rb = Wuu[o] + B * B * P;
       if (!(Rb > 0.0)) return false;
-      const double iR = 1.0 / Rb;
+      const double iR = recip(Rb);
       const double Sb = (k > 0) ? Wxu[o] + A * P * B : 0.0;
       const double sb = (has_r ? r_[o] : 0.0) + B * Pbp;
       K_[o] = -Sb * iR;

@@ -203,7 +203,7 @@ __device__ __forceinline__ void bfgs_block(int n, double& w11, double& w12, doub
   const double kappa = fmin(sWs, sr);
   if (!(kappa > eps_m)) return;
   // both reciprocals from one division (both factors exceed eps_m here)
-  const double inv = 1.0 / (sWs * sr);
+  const double inv = rcp_newton(sWs * sr);
   const double isWs = sr * inv, isr = sWs * inv;
   w11 = w11 - Ws1 * Ws1 * isWs + r1 * r1 * isr;
   if (n == 2) {
