@@ -191,77 +191,68 @@ MC_HD bool as_backward(int N, int64_t ld, uint64_t fixed, bool has_r,
 }
 
 // Forward sweep (subspace minimiser z, states, dynamics multipliers) fused with
-// the ratio test over the free inputs: returns the blocking stage (-1 if none),
-// its side and the step length alpha.
-MC_HD int as_forward(int N, int64_t ld, uint64_t fixed, const double* __restrict__ A_,
+// the ratio test over the free inputs and with the working set's bound
+// multipliers: returns the blocking stage (-1 if none), its side and the step
+// length alpha.  On the free stages du becomes z and the previous du is kept
+// in z_ (the caller steps from it by alpha when a bound blocks).  On the fixed
+// stages the multiplier of the active bound comes from stationarity in du_k
+// at (dx_k, mu_k), all at hand in the sweep; nul, nuu receive them (0 on free
+// stages) and worst the stage with the most negative one below -mult_tol (-1:
+// none).  They are the QP's when nothing blocks and none is negative.
+MC_HD int as_forward(int N, int64_t ld, uint64_t fixed, uint64_t lo, bool has_r,
+                     double mult_tol, const double* __restrict__ A_,
                      const double* __restrict__ B_, const double* __restrict__ b_,
                      const double* __restrict__ P_, const double* __restrict__ p_,
                      const double* __restrict__ K_, const double* __restrict__ kf_,
                      const double* __restrict__ lb_, const double* __restrict__ ub_,
-                     const double* __restrict__ du_, double* __restrict__ z_,
-                     double* __restrict__ dx_, double* __restrict__ mu_, double& alpha,
-                     bool& block_lo) {
+                     const double* __restrict__ r_, const double* __restrict__ Wxu,
+                     const double* __restrict__ Wuu, double* __restrict__ du_,
+                     double* __restrict__ z_, double* __restrict__ dx_,
+                     double* __restrict__ mu_, double* __restrict__ nul_,
+                     double* __restrict__ nuu_, double& alpha, bool& block_lo, int& worst) {
   double dx = 0.0;
   alpha = 1.0;
   int block = -1;
   block_lo = false;
-#pragma unroll 2
-  for (int k = 0; k < N; ++k) {
-    const int64_t o = k * ld;
-    const double A = (k > 0) ? A_[o] : 0.0;
-    const double z = K_[o] * dx + kf_[o];
-    const double dxn = A * dx + B_[o] * z + b_[o];
-    z_[o] = z;
-    dx_[o + ld] = dxn;
-    mu_[o] = -(P_[o + ld] * dxn + p_[o + ld]);
-    dx = dxn;
-    if ((fixed >> k) & 1ull) continue;
-    const double du = du_[o];
-    const double lb = lb_[o], ub = ub_[o];
-    const double pk = z - du;
-    if (pk < 0.0 && z < lb) {
-      const double t = (lb - du) / pk;
-      if (t < alpha) { alpha = t; block = k; block_lo = true; }
-    } else if (pk > 0.0 && z > ub) {
-      const double t = (ub - du) / pk;
-      if (t < alpha) { alpha = t; block = k; block_lo = false; }
-    }
-  }
-  return block;
-}
-
-// At a subspace minimiser: du = z on the free stages, and the working-set
-// multipliers; returns the stage with the most negative one (-1: optimal).
-// The bound multipliers of the working set are written too (0 on free
-// stages): when no multiplier is negative they are the QP's.
-MC_HD int as_multipliers(int N, int64_t ld, uint64_t fixed, uint64_t lo, bool has_r,
-                         double mult_tol, const double* __restrict__ B_,
-                         const double* __restrict__ r_, const double* __restrict__ Wxu,
-                         const double* __restrict__ Wuu, const double* __restrict__ z_,
-                         const double* __restrict__ dx_, const double* __restrict__ mu_,
-                         double* __restrict__ du_, double* __restrict__ nul_,
-                         double* __restrict__ nuu_) {
-  int worst = -1;
+  worst = -1;
   double worst_val = -mult_tol;
 #pragma unroll 2
   for (int k = 0; k < N; ++k) {
     const int64_t o = k * ld;
-    const bool f = (fixed >> k) & 1ull;
-    const double du = f ? du_[o] : z_[o];
-    du_[o] = du;
+    const double A = (k > 0) ? A_[o] : 0.0;
+    const double B = B_[o];
+    const double z = K_[o] * dx + kf_[o];
+    const double dxn = A * dx + B * z + b_[o];
+    const double mu = -(P_[o + ld] * dxn + p_[o + ld]);
+    dx_[o + ld] = dxn;
+    mu_[o] = mu;
+    const double du = du_[o];
     double nl = 0.0, nu = 0.0;
-    if (f) {
-      const double cross = (k > 0) ? Wxu[o] * dx_[o] : 0.0;
-      const double v = Wuu[o] * du + cross + (has_r ? r_[o] : 0.0) - mu_[o] * B_[o];
+    if ((fixed >> k) & 1ull) {
+      const double cross = (k > 0) ? Wxu[o] * dx : 0.0;
+      const double v = Wuu[o] * du + cross + (has_r ? r_[o] : 0.0) - mu * B;
       const bool at_lo = (lo >> k) & 1ull;
       const double lam = at_lo ? v : -v;
       if (lam < worst_val) { worst_val = lam; worst = k; }
       if (at_lo) nl = v; else nu = -v;
+    } else {
+      z_[o] = du;
+      du_[o] = z;
+      const double lb = lb_[o], ub = ub_[o];
+      const double pk = z - du;
+      if (pk < 0.0 && z < lb) {
+        const double t = (lb - du) / pk;
+        if (t < alpha) { alpha = t; block = k; block_lo = true; }
+      } else if (pk > 0.0 && z > ub) {
+        const double t = (ub - du) / pk;
+        if (t < alpha) { alpha = t; block = k; block_lo = false; }
+      }
     }
     nul_[o] = nl;
     nuu_[o] = nu;
+    dx = dxn;
   }
-  return worst;
+  return block;
 }
 
 // Working set at the start (bounds active at the current iterate, du on them)
@@ -338,15 +329,18 @@ MC_HD QpResult qp_active_set_from(const Ws& w, int N, bool has_r, int max_it, ui
     }
     double alpha;
     bool block_lo;
-    const int block = as_forward(N, ld, fixed, A_, B_, b_, P_, p_, K_, kf_, lb_, ub_, du_, z_,
-                                 dx_, mu_, alpha, block_lo);
+    int worst;
+    const int block = as_forward(N, ld, fixed, lo, has_r, mult_tol, A_, B_, b_, P_, p_, K_,
+                                 kf_, lb_, ub_, r_, Wxu, Wuu, du_, z_, dx_, mu_, nul_, nuu_,
+                                 alpha, block_lo, worst);
     if (block >= 0) {
+      // step from the previous du (kept in z_) towards z (now in du_)
       if (alpha < 0.0) alpha = 0.0;
       for (int k = 0; k < N; ++k) {
         if ((fixed >> k) & 1ull) continue;
         const int64_t o = k * ld;
-        const double du = du_[o];
-        du_[o] = du + alpha * (z_[o] - du);
+        const double du = z_[o];
+        du_[o] = du + alpha * (du_[o] - du);
       }
       if (block_lo) {
         lo |= 1ull << block;
@@ -357,8 +351,6 @@ MC_HD QpResult qp_active_set_from(const Ws& w, int N, bool has_r, int max_it, ui
       }
       continue;
     }
-    const int worst = as_multipliers(N, ld, fixed, lo, has_r, mult_tol, B_, r_, Wxu, Wuu, z_,
-                                     dx_, mu_, du_, nul_, nuu_);
     if (worst < 0) {
       res.status = 0;
       break;
@@ -366,7 +358,7 @@ MC_HD QpResult qp_active_set_from(const Ws& w, int N, bool has_r, int max_it, ui
     lo &= ~(1ull << worst);
     up &= ~(1ull << worst);
   }
-  // the multiplier pass wrote the bound multipliers of an optimal working set;
+  // the forward sweep wrote the bound multipliers of an optimal working set;
   // at the iteration limit they follow from the last one
   if (res.status != 0)
     as_bound_multipliers(N, ld, lo, up, has_r, B_, r_, Wxu, Wuu, du_, dx_, mu_, nul_, nuu_);
