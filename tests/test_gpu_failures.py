@@ -148,3 +148,33 @@ def test_invalid_parameters_are_rejected_before_any_launch(field, value):
     with pytest.raises(mc.McError) as e:
         mc.MonteCarlo(m, w["nmpc"], 4, w["seed"])
     assert e.value.status == mc.MC_EINVAL
+
+
+def test_nmpc_gradient_of_trajectories_that_go_non_finite():
+    """The NMPC-weight gradient when extreme noise drives some trajectories
+    non-finite part-way: the persistent schedule's records then end at the
+    sample where the trajectory stopped.  Both schedules flag the same
+    trajectories, give them Phi and tangents NaN, and agree bit for bit on
+    the others."""
+    w = W.get("cstr_100x120_N20_fp64")
+    m = dict(w["model"], n_steps=30)
+    m["sigma"] = [s * 200.0 for s in m["sigma"]]
+    c = dict(w["nmpc"], Ru=0.2, Qn=1.0)
+    n = 128
+    out = {}
+    for sched in ("static", "persistent"):
+        h = mc.MonteCarlo(m, dict(c, schedule=sched), n, w["seed"])
+        h.nmpc_grad()
+        st = h.stats()
+        out[sched] = (h.phi(), h.grad(), h.counters(), st)
+        h.close()
+    (p0, g0, c0, s0), (p1, g1, c1, s1) = out["static"], out["persistent"]
+    bad = c0["nonfinite"] > 0
+    assert 0 < bad.sum() < n, bad.sum()
+    assert s1["n_nonfinite"] == bad.sum()
+    assert np.all(np.isnan(p1[bad])) and np.all(np.isnan(g1[bad]))
+    assert np.array_equal(p0, p1, equal_nan=True)
+    assert np.array_equal(g0, g1, equal_nan=True)
+    for k in c0:
+        assert np.array_equal(c0[k], c1[k]), k
+    assert np.all(np.isfinite(g1[~bad]))
