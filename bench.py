@@ -95,7 +95,7 @@ def nmpc_pipe_ops(cfg_model, cfg_ctrl, n_traj, st, w):
     first_evals = n_traj * N + (st["n_ocp"] - n_traj) * min(N, 2)   # warm starts reuse N-2
     ops = (first_evals + st["ls_trials"] * N) * per_interval
     ops += (st["n_ocp"] + st["ls_trials"]) * nrk * OPS_COV_STEP   # interval 0 of each evaluation
-    ops += st["qp_iters"] * N * (OPS_QP_STAGE + w["div"])
+    ops += st["qp_iters"] * N * (OPS_QP_STAGE + w.get("rcp", w["div"]))   # the pivot's reciprocal
     ops += st["sqp_iters"] * N * (OPS_SQP_STAGE + OPS_ACCEPT_STAGE + 3 * w["div"])
     ops += st["ls_trials"] * N * OPS_TRIAL_STAGE
     em = OPS_EM + w["exp_table"] + w["div"] + 2 * (8 + w["log"] + w["sqrt"] + w["sincospi"])
