@@ -146,3 +146,12 @@ def test_warp_trace_layout_and_null_arguments(L):
     assert int(re.search(r"kWarpTraceWords = (\d+)", src).group(1)) == mc.WARP_TRACE_WORDS
     nw = C.c_int64(7)
     assert L.mc_copy_warp_trace(None, None, 0, C.byref(nw)) == mc.MC_EINVAL
+
+
+def test_new_handle_calls_reject_a_null_handle(L):
+    """The gradient's record budget and the per-warp record reject a null
+    handle before touching the device."""
+    assert L.mc_set_grad_record_budget(None, 0) == mc.MC_EINVAL
+    nw = C.c_int64(0)
+    assert L.mc_copy_warp_trace(None, None, 0, C.byref(nw)) == mc.MC_EINVAL
+    assert L.mc_copy_warp_trace(None, None, -1, C.byref(nw)) == mc.MC_EINVAL
